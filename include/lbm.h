@@ -1,0 +1,205 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the well-balanced
+ * phase-field lattice Boltzmann model of incompressible binary fluids
+ * (Ju, Liu, Yan, Bao, Sun, Guo; arXiv:2311.10827).
+ *
+ * Naming.  As in the paper, f is the Cahn-Hilliard (CH) population
+ * (Eq. BGK; velocity-free equilibrium Eq. H_i, convection source Eq. F_i)
+ * and g the hydrodynamic population (Eq. BGK-NS; equilibrium Eq. G_i,
+ * force Eq. GGi).  Some texts swap the letters; this library does not.
+ *
+ * One time step (Section 2.3) advances both populations:
+ *   phi = sum_i f_i; mu = psi'(phi) - kappa lap(phi) (Eq. chemical_potencial);
+ *   grad(phi), grad(mu) with the isotropic stencil (Eq. gradient), lap with
+ *   Eq. Laplace; rho, nu linear in phi (Eq. vis); F = -phi grad(mu) + G;
+ *   rho u = sum c_i g_i + F/2; p from the moment below Eq. GGi;
+ *   S = u.grad(phi); f_i* = f_i - (f_i - f_i^eq)/tau_f + w_i b_i (1.5 S - 0.5 S_prev);
+ *   g_i* = g_i - (g_i - g_i^eq)/tau_g + G_i; then periodic streaming.
+ * The (1/2) dt^2 d_t F_i term of Eq. BGK is read as a backward difference in
+ * time, which is why S of the previous step is part of the state.
+ *
+ * Conventions.
+ *  - Every function returns LBM_OK (0) or a negative LBM_ERR_* code; no C++
+ *    exception crosses this boundary.
+ *  - An error that the device reports asynchronously (a non-finite value
+ *    seen by the diagnostics, a CUDA fault) is recorded in the context and
+ *    returned by the next call that can fail, then cleared ("sticky until
+ *    read").  A CUDA error leaves the context unusable: destroy it.
+ *  - Pointers passed in are never retained.  Host arrays are caller-owned
+ *    and only read or written during the call.  Device arrays passed with
+ *    on_device = 1 must be device memory of the context's GPU and must stay
+ *    valid until the context's stream has passed the call.
+ *  - Field layout: scalar fields are [nz][ny][nx] (x fastest), node index
+ *    n = (z*ny + y)*nx + x, N = nx*ny*nz.  Vector fields are [D][N].
+ *    Populations are [Q][N].  All boundaries are periodic (Section 3).
+ *  - Lattice units: dx = dt = 1, cs^2 = 1/3.
+ *  - The context owns all its device memory (allocated by lbm_create, freed
+ *    by lbm_destroy).  Work is issued on the CUDA stream given to
+ *    lbm_create (NULL = the legacy default stream).
+ */
+#ifndef WB_LBM_H
+#define WB_LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define LBM_OK               0
+#define LBM_ERR_INVALID_ARG (-1) /* bad pointer, size, parameter or call order */
+#define LBM_ERR_OOM         (-2) /* device or host allocation failed */
+#define LBM_ERR_CUDA        (-3) /* a CUDA runtime call failed (no GPU, fault) */
+#define LBM_ERR_NONFINITE   (-4) /* the diagnostics saw NaN/Inf in the fields */
+#define LBM_ERR_TIMEOUT     (-5) /* a bounded device wait gave up */
+#define LBM_ERR_STATE       (-6) /* context not initialised (lbm_init_phi first) */
+
+/* Grid: nz = 1 for D2Q9.  Every boundary is periodic. */
+typedef struct {
+    int nx, ny, nz;
+} lbm_grid;
+
+/* Lattices: D2Q9 for both populations (Eq. eq:ci, weights below Eq. H_iyang);
+ * D3Q19 (not in the paper) with the same equilibria, sources and stencils. */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* Precision of storage and arithmetic.  LBM_FP64: FP64 throughout (parity
+ * form).  LBM_FP32: FP32 populations and arithmetic; diagnostics in FP64. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
+
+/* The paper's statement of the problem (Section 2 and Section 3):
+ *   W      interface thickness (Eq. beta)
+ *   M      mobility M_phi (Eq. CH_equation, Eq. mobility)
+ *   alpha  the adjustable CH equilibrium parameter (Eq. H_i)
+ *   sigma  surface tension (Eq. suiface_tension); kappa and beta follow:
+ *          kappa = 3 W sigma / (2 dphi^2), beta = 12 sigma / (W dphi^4)
+ *   phi_l, phi_v   bulk order parameters (default 1 and 0)
+ *   rho_l, rho_v   bulk densities; rho is linear in phi
+ *   nu_l, nu_v     bulk kinematic viscosities; nu is linear in phi (Eq. vis),
+ *                  tau_g = 1/2 + nu / cs^2 node by node
+ *   body_force     G in F = F_s + G (text after Eq. GGi)
+ *   tau_f  0: derive tau_f = 1/2 + M / (cs^2 alpha) (Eq. mobility);
+ *          > 1/2: use it and derive alpha = M / (cs^2 (tau_f - 1/2))
+ *   precision      an lbm_precision value
+ *   diag_every     0: no automatic diagnostics; k > 0: lbm_step fuses the
+ *                  diagnostics reduction into every k-th step and records a
+ *                  non-finite value as LBM_ERR_NONFINITE */
+typedef struct {
+    double W, M, alpha, sigma;
+    double phi_l, phi_v;
+    double rho_l, rho_v, nu_l, nu_v;
+    double body_force[3];
+    double tau_f;
+    int precision;
+    int diag_every;
+} lbm_params;
+
+/* Diagnostics of the state at time `step` (all sums in FP64):
+ *   sum_phi         sum over nodes of phi
+ *   kinetic_energy  E = 1/2 sum rho |u|^2 (the paper's E, Section 3.1)
+ *   u_max           max |u| (spurious velocity in the equilibrium tests)
+ *   mu_min, mu_max  range of the chemical potential
+ *   budget          sum of (1.5 S - 0.5 S_prev): the exact change of the
+ *                   phi sum over the next step is -budget, because
+ *                   sum_i f_i^eq = phi and sum_i F_i = -S (Eq. sumfeqandF)
+ *   nonfinite       1 if any node had a NaN/Inf field value */
+typedef struct {
+    double sum_phi, kinetic_energy, u_max, mu_min, mu_max, budget;
+    long long step;
+    int nonfinite;
+} lbm_diag;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *out with the paper's defaults (W 4, M 0.1, alpha 1, sigma 1e-3,
+ * phi_l 1, phi_v 0, rho_l 10, rho_v 1, nu_l = nu_v = 0.1, no body force,
+ * tau_f derived, FP32, no automatic diagnostics).  Errors: INVALID_ARG if
+ * out is NULL. */
+int lbm_params_default(lbm_params *out);
+
+/* Validate the problem, derive kappa, beta and tau_f (Eqs. beta,
+ * suiface_tension, mobility) and allocate the device state (double-buffered
+ * f and g, S_prev, work buffers) on the current CUDA device.  `cuda_stream`
+ * is a cudaStream_t (NULL = legacy default stream) on which all later work is
+ * issued.  Errors: INVALID_ARG (NULL pointers, non-positive sizes, nz != 1
+ * for D2Q9, W <= 0, sigma < 0, M <= 0 or alpha <= 0 when tau_f is derived,
+ * tau_f <= 1/2, phi_l == phi_v, rho <= 0, nu <= 0, unknown precision),
+ * OOM, CUDA (no usable GPU).  Validation happens before any CUDA call, so a
+ * host without a GPU reports INVALID_ARG for a bad problem. */
+int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params,
+               void *cuda_stream, lbm_ctx **out);
+
+/* Set the initial condition from an order-parameter field phi[N] (FP64):
+ * f = f^eq(phi, mu(phi)) (Eq. H_i), g = 0 (p = 0, u = 0), S_prev = 0, time 0.
+ * on_device = 0: host array (copied, the call returns once it is read);
+ * on_device = 1: device array.  Errors: INVALID_ARG, CUDA. */
+int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device);
+
+/* Advance n >= 0 time steps, asynchronously on the context's stream (one
+ * fused stream-collide kernel per step; a CUDA graph for long runs).
+ * Returns a recorded error, if any.  Errors: STATE, INVALID_ARG, CUDA,
+ * NONFINITE (recorded by an earlier fused diagnostics step). */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* Macroscopic fields at the current time (FP64 outputs): phi[N], p[N]
+ * (hydrodynamic pressure), u[D*N] ([D][N]), mu[N].  Any output may be NULL.
+ * on_device = 0: host arrays (the call synchronises the stream);
+ * on_device = 1: device arrays (asynchronous).  Errors: STATE, CUDA. */
+int lbm_moments(lbm_ctx *ctx, double *phi, double *p, double *u, double *mu,
+                int on_device);
+
+/* Diagnostics of the current state (synchronises).  Errors: STATE, CUDA,
+ * INVALID_ARG.  A non-finite field is reported through out->nonfinite (the
+ * call itself still returns LBM_OK). */
+int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
+
+/* Diagnostics recorded by the most recent fused diagnostics step of
+ * lbm_step (diag_every > 0), describing the state at out->step.  Synchronises.
+ * Errors: STATE if none was recorded yet, CUDA. */
+int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out);
+
+/* Exchange the full state in the paper's convention, FP64: f[Q*N], g[Q*N]
+ * hold f_i(x,t), g_i(x,t) (after streaming, before collision) and
+ * S_prev[N] holds u.grad(phi) of step t-1.  lbm_set_state also sets the
+ * time to `step` and marks the context initialised.  on_device selects host
+ * (synchronous) or device (asynchronous) arrays.  Errors: STATE (get before
+ * init), INVALID_ARG, CUDA. */
+int lbm_get_state(lbm_ctx *ctx, double *f, double *g, double *S_prev, int on_device);
+int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g,
+                  const double *S_prev, long long step, int on_device);
+
+/* Checkpoint to / restore from a host buffer in the library's own format
+ * (header + raw device state at the context's precision, so a restore is
+ * bit-exact).  lbm_save with buf == NULL stores the required size in *bytes.
+ * lbm_load checks that grid, lattice and precision match.  Errors:
+ * INVALID_ARG (size or header mismatch), STATE, CUDA. */
+int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes);
+int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Wait for the context's stream; returns a recorded error, if any. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Current time step (number of steps taken since the initial condition). */
+long long lbm_time(const lbm_ctx *ctx);
+
+/* kappa, beta, tau_f and alpha actually used.  Errors: INVALID_ARG. */
+int lbm_derived(const lbm_ctx *ctx, double out[4]);
+
+/* Host-side fault injection for tests: write `value` into population f
+ * (field 0) or g (field 1), direction i, node n of the current state.
+ * Errors: STATE, INVALID_ARG, CUDA. */
+int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value);
+
+/* Release the context and its device memory (synchronises first).
+ * NULL-safe. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Static description of an error code. */
+const char *lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WB_LBM_H */

@@ -1,0 +1,681 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation and
+// derivation, device buffers, kernel sequencing (with a CUDA graph for long
+// runs), diagnostics, state exchange and checkpoints.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace wblbm;
+
+namespace {
+
+constexpr double CS2 = 1.0 / 3.0;
+constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: ping-pong)
+
+// D2Q9 velocities (order of Eq. eq:ci), used on the host only for
+// lbm_debug_poke.
+constexpr int HCX[9] = {0, 0, 1, 0, -1, 1, -1, -1, 1};
+constexpr int HCY[9] = {0, -1, 0, 1, 0, 1, 1, -1, -1};
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_grid grid;
+    int lattice;
+    lbm_params prm;
+    double kappa, beta, tau_f, alpha;
+    int Q, D;
+    long long N;
+    size_t esz;  // bytes per stored population value
+    void *f[2], *g[2], *S;
+    int cur;     // f[cur], g[cur] hold the current state
+    double *aux;         // N doubles (initial chemical potential)
+    double *stage;       // (3 + D) N doubles, host moment staging (lazy)
+    DiagPartial *partials;
+    DiagPartial *dres;   // device: [0] on-demand diagnostics, [1] last fused
+    DiagPartial *hres;   // pinned host copy of dres
+    int npart;
+    cudaStream_t stream;
+    cudaStream_t cap;    // private stream used for graph capture
+    cudaEvent_t diag_ev; // recorded after a fused diagnostics copy
+    int diag_pending;
+    long long last_diag_step;
+    int has_last_diag;
+    int device;
+    long long step;
+    int initialized;
+    int err;             // sticky error (returned once, then cleared)
+    LaunchShape shape;
+    StepParams<double> pd;
+    StepParams<float> pf;
+    cudaGraphExec_t gexec;
+    int gexec_valid;
+};
+
+namespace {
+
+int fail_cuda(lbm_ctx *c, cudaError_t e)
+{
+    if (e == cudaSuccess) return LBM_OK;
+    if (c) c->err = LBM_ERR_CUDA;
+    return LBM_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, e_);     \
+    } while (0)
+
+int take_err(lbm_ctx *c)
+{
+    int e = c->err;
+    if (e != LBM_ERR_CUDA) c->err = LBM_OK;  // CUDA errors stay: the context is unusable
+    return e;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+int validate(const lbm_grid *g, int lattice, const lbm_params *p)
+{
+    if (!g || !p) return LBM_ERR_INVALID_ARG;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_ERR_INVALID_ARG;
+    if (lattice != LBM_D2Q9) return LBM_ERR_INVALID_ARG;  // D3Q19: not built yet
+    if (lattice == LBM_D2Q9 && g->nz != 1) return LBM_ERR_INVALID_ARG;
+    if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->W) || !isfinite(p->sigma) || p->sigma < 0.0) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->M)) return LBM_ERR_INVALID_ARG;
+    if (p->tau_f == 0.0) {
+        if (!finite_pos(p->alpha)) return LBM_ERR_INVALID_ARG;
+    } else if (!isfinite(p->tau_f) || p->tau_f <= 0.5) {
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (!isfinite(p->phi_l) || !isfinite(p->phi_v) || p->phi_l == p->phi_v)
+        return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->rho_l) || !finite_pos(p->rho_v)) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->nu_l) || !finite_pos(p->nu_v)) return LBM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(p->body_force[a])) return LBM_ERR_INVALID_ARG;
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return LBM_ERR_INVALID_ARG;
+    if (p->diag_every < 0) return LBM_ERR_INVALID_ARG;
+    return LBM_OK;
+}
+
+template <typename T>
+void fill_params(StepParams<T> &P, const lbm_ctx *c)
+{
+    const lbm_params &p = c->prm;
+    const double dphi = p.phi_l - p.phi_v;
+    P.nx = c->grid.nx;
+    P.ny = c->grid.ny;
+    P.nz = c->grid.nz;
+    P.N = c->N;
+    P.kappa = (T)c->kappa;
+    P.beta = (T)c->beta;
+    P.phil = (T)p.phi_l;
+    P.phiv = (T)p.phi_v;
+    P.phibar = (T)(0.5 * (p.phi_l + p.phi_v));
+    P.alpha = (T)c->alpha;
+    P.inv_tauf = (T)(1.0 / c->tau_f);
+    P.rhov = (T)p.rho_v;
+    P.drho = (T)((p.rho_l - p.rho_v) / dphi);
+    P.nuv = (T)p.nu_v;
+    P.dnu = (T)((p.nu_l - p.nu_v) / dphi);
+    for (int a = 0; a < 3; ++a) P.G[a] = (T)p.body_force[a];
+}
+
+const void *params_ptr(const lbm_ctx *c)
+{
+    return c->prm.precision == LBM_FP64 ? (const void *)&c->pd : (const void *)&c->pf;
+}
+
+int set_device(lbm_ctx *ctx)
+{
+    CK(cudaSetDevice(ctx->device));
+    return LBM_OK;
+}
+
+// one pass over the current state
+int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p, double *o_u,
+             double *o_mu)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.f_src = ctx->f[ctx->cur];
+    a.g_src = ctx->g[ctx->cur];
+    a.f_dst = ctx->f[ctx->cur ^ 1];
+    a.g_dst = ctx->g[ctx->cur ^ 1];
+    a.S = ctx->S;
+    a.out_phi = o_phi;
+    a.out_p = o_p;
+    a.out_u = o_u;
+    a.out_mu = o_mu;
+    a.partials = ctx->partials;
+    CK(d2q9_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, st));
+    return LBM_OK;
+}
+
+// A graph of GRAPH_STEPS plain steps starting from cur = 0 (ends at cur = 0).
+int ensure_graph(lbm_ctx *ctx)
+{
+    if (ctx->gexec_valid) return LBM_OK;
+    const int saved = ctx->cur;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = LBM_OK;
+    ctx->cur = 0;
+    for (int k = 0; k < GRAPH_STEPS && rc == LBM_OK; ++k) {
+        rc = run_pass(ctx, PASS_STATE, ctx->cap, nullptr, nullptr, nullptr, nullptr);
+        ctx->cur ^= 1;
+    }
+    ctx->cur = saved;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &graph);
+    if (rc != LBM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    ctx->gexec_valid = 1;
+    return LBM_OK;
+}
+
+void poll_diag(lbm_ctx *ctx, bool wait)
+{
+    if (!ctx->diag_pending) return;
+    cudaError_t e = wait ? cudaEventSynchronize(ctx->diag_ev) : cudaEventQuery(ctx->diag_ev);
+    if (e == cudaErrorNotReady) return;
+    if (e != cudaSuccess) {
+        ctx->err = LBM_ERR_CUDA;
+        return;
+    }
+    ctx->diag_pending = 0;
+    if (ctx->hres[1].nonfinite != 0.0 && ctx->err == LBM_OK) ctx->err = LBM_ERR_NONFINITE;
+}
+
+void fill_diag(const DiagPartial &r, long long step, lbm_diag *out)
+{
+    out->sum_phi = r.sum_phi;
+    out->kinetic_energy = r.E;
+    out->u_max = sqrt(r.u2max);
+    out->mu_min = r.mu_min;
+    out->mu_max = r.mu_max;
+    out->budget = r.budget;
+    out->step = step;
+    out->nonfinite = r.nonfinite != 0.0;
+}
+
+void free_all(lbm_ctx *c)
+{
+    if (c->gexec_valid) cudaGraphExecDestroy(c->gexec);
+    void *dev[] = {c->f[0], c->f[1], c->g[0], c->g[1], c->S, c->aux, c->stage, c->partials, c->dres};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (c->hres) cudaFreeHost(c->hres);
+    if (c->diag_ev) cudaEventDestroy(c->diag_ev);
+    if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_params_default(lbm_params *out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    memset(out, 0, sizeof *out);
+    out->W = 4.0;
+    out->M = 0.1;
+    out->alpha = 1.0;
+    out->sigma = 1e-3;
+    out->phi_l = 1.0;
+    out->phi_v = 0.0;
+    out->rho_l = 10.0;
+    out->rho_v = 1.0;
+    out->nu_l = 0.1;
+    out->nu_v = 0.1;
+    out->tau_f = 0.0;
+    out->precision = LBM_FP32;
+    out->diag_every = 0;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void *cuda_stream,
+               lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(grid, lattice, params);
+    if (rc != LBM_OK) return rc;
+
+    lbm_ctx *ctx = (lbm_ctx *)calloc(1, sizeof(lbm_ctx));
+    if (!ctx) return LBM_ERR_OOM;
+    ctx->grid = *grid;
+    ctx->lattice = lattice;
+    ctx->prm = *params;
+    ctx->Q = 9;
+    ctx->D = 2;
+    ctx->N = (long long)grid->nx * grid->ny * grid->nz;
+    ctx->esz = params->precision == LBM_FP64 ? 8 : 4;
+    ctx->stream = (cudaStream_t)cuda_stream;
+
+    // Eqs. beta and suiface_tension solved for kappa and beta; Eq. mobility.
+    const double d2 = (params->phi_l - params->phi_v) * (params->phi_l - params->phi_v);
+    ctx->kappa = 3.0 * params->W * params->sigma / (2.0 * d2);
+    ctx->beta = 12.0 * params->sigma / (params->W * d2 * d2);
+    if (params->tau_f == 0.0) {
+        ctx->alpha = params->alpha;
+        ctx->tau_f = 0.5 + params->M / (CS2 * params->alpha);
+    } else {
+        ctx->tau_f = params->tau_f;
+        ctx->alpha = params->M / (CS2 * (params->tau_f - 0.5));
+    }
+    fill_params(ctx->pd, ctx);
+    fill_params(ctx->pf, ctx);
+
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    int nsm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) {
+        free(ctx);
+        return LBM_ERR_CUDA;
+    }
+    ctx->shape = d2q9_shape(grid->nx, grid->ny, nsm);
+    ctx->npart = ctx->shape.nblocks;
+
+    const size_t N = (size_t)ctx->N, Q = (size_t)ctx->Q;
+    bool oom = false;
+    auto dalloc = [&](void **p, size_t bytes) {
+        if (oom) return;
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            *p = nullptr;
+            oom = true;
+        }
+    };
+    dalloc(&ctx->f[0], Q * N * ctx->esz);
+    dalloc(&ctx->f[1], Q * N * ctx->esz);
+    dalloc(&ctx->g[0], Q * N * ctx->esz);
+    dalloc(&ctx->g[1], Q * N * ctx->esz);
+    dalloc(&ctx->S, N * ctx->esz);
+    dalloc((void **)&ctx->aux, N * sizeof(double));
+    dalloc((void **)&ctx->partials, (size_t)ctx->npart * sizeof(DiagPartial));
+    dalloc((void **)&ctx->dres, 2 * sizeof(DiagPartial));
+    if (!oom && cudaMallocHost((void **)&ctx->hres, 2 * sizeof(DiagPartial)) != cudaSuccess)
+        oom = true;
+    if (!oom && (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&ctx->diag_ev, cudaEventDisableTiming) != cudaSuccess))
+        oom = true;
+    if (oom) {
+        cudaGetLastError();  // clear the allocation error
+        free_all(ctx);
+        free(ctx);
+        return LBM_ERR_OOM;
+    }
+    memset(ctx->hres, 0, 2 * sizeof(DiagPartial));
+    *out = ctx;
+    return LBM_OK;
+}
+
+int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
+{
+    if (!ctx || !phi) return LBM_ERR_INVALID_ARG;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    const size_t N = (size_t)ctx->N;
+    const double *src = phi;
+    double *tmp = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc((void **)&tmp, N * sizeof(double)));
+        cudaError_t e = cudaMemcpyAsync(tmp, phi, N * sizeof(double), cudaMemcpyHostToDevice,
+                                        ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return fail_cuda(ctx, e);
+        }
+        src = tmp;
+    }
+    cudaError_t e = d2q9_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0], ctx->g[0],
+                              ctx->S, ctx->stream);
+    if (tmp) {
+        cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+        cudaFree(tmp);
+        if (e == cudaSuccess) e = e2;
+    }
+    CK(e);
+    ctx->cur = 0;
+    ctx->step = 0;
+    ctx->initialized = 1;
+    ctx->has_last_diag = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *ctx, int n)
+{
+    if (!ctx || n < 0) return LBM_ERR_INVALID_ARG;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (int rc = set_device(ctx)) return rc;
+    poll_diag(ctx, false);
+    if (ctx->err) return take_err(ctx);
+    const int de = ctx->prm.diag_every;
+    int left = n;
+    while (left > 0) {
+        if (de > 0 && ctx->step % de == 0) {
+            // fused diagnostics step: reduce the partials, copy the record
+            int rc = run_pass(ctx, PASS_STATE | PASS_DIAG, ctx->stream, nullptr, nullptr,
+                              nullptr, nullptr);
+            if (rc) return rc;
+            CK(diag_reduce(ctx->partials, ctx->npart, ctx->dres + 1, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->hres + 1, ctx->dres + 1, sizeof(DiagPartial),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaEventRecord(ctx->diag_ev, ctx->stream));
+            ctx->diag_pending = 1;
+            ctx->has_last_diag = 1;
+            ctx->last_diag_step = ctx->step;
+            ctx->cur ^= 1;
+            ctx->step += 1;
+            left -= 1;
+            continue;
+        }
+        // plain steps up to the next diagnostics step
+        long long run = left;
+        if (de > 0) {
+            const long long to_diag = de - ctx->step % de;
+            if (to_diag < run) run = to_diag;
+        }
+        if (run >= GRAPH_STEPS) {
+            if (ctx->cur == 1) {
+                int rc = run_pass(ctx, PASS_STATE, ctx->stream, nullptr, nullptr, nullptr, nullptr);
+                if (rc) return rc;
+                ctx->cur = 0;
+                ctx->step += 1;
+                left -= 1;
+                run -= 1;
+            }
+            if (run >= GRAPH_STEPS) {
+                if (int rc = ensure_graph(ctx)) return rc;
+                const long long reps = run / GRAPH_STEPS;
+                for (long long r = 0; r < reps; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+                ctx->step += reps * GRAPH_STEPS;
+                left -= (int)(reps * GRAPH_STEPS);
+                run -= reps * GRAPH_STEPS;
+            }
+        }
+        for (long long k = 0; k < run; ++k) {
+            int rc = run_pass(ctx, PASS_STATE, ctx->stream, nullptr, nullptr, nullptr, nullptr);
+            if (rc) return rc;
+            ctx->cur ^= 1;
+            ctx->step += 1;
+            left -= 1;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *ctx, double *phi, double *p, double *u, double *mu, int on_device)
+{
+    if (!ctx) return LBM_ERR_INVALID_ARG;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    const size_t N = (size_t)ctx->N;
+    if (on_device) return run_pass(ctx, PASS_MACROS, ctx->stream, phi, p, u, mu);
+    if (!ctx->stage) CK(cudaMalloc((void **)&ctx->stage, (3 + ctx->D) * N * sizeof(double)));
+    double *s_phi = ctx->stage, *s_p = s_phi + N, *s_mu = s_p + N, *s_u = s_mu + N;
+    int rc = run_pass(ctx, PASS_MACROS, ctx->stream, phi ? s_phi : nullptr, p ? s_p : nullptr,
+                      u ? s_u : nullptr, mu ? s_mu : nullptr);
+    if (rc) return rc;
+    const size_t b = N * sizeof(double);
+    if (phi) CK(cudaMemcpyAsync(phi, s_phi, b, cudaMemcpyDeviceToHost, ctx->stream));
+    if (p) CK(cudaMemcpyAsync(p, s_p, b, cudaMemcpyDeviceToHost, ctx->stream));
+    if (mu) CK(cudaMemcpyAsync(mu, s_mu, b, cudaMemcpyDeviceToHost, ctx->stream));
+    if (u) CK(cudaMemcpyAsync(u, s_u, ctx->D * b, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out)
+{
+    if (!ctx || !out) return LBM_ERR_INVALID_ARG;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    int rc = run_pass(ctx, PASS_DIAG, ctx->stream, nullptr, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    CK(diag_reduce(ctx->partials, ctx->npart, ctx->dres, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    fill_diag(ctx->hres[0], ctx->step, out);
+    return LBM_OK;
+}
+
+int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out)
+{
+    if (!ctx || !out) return LBM_ERR_INVALID_ARG;
+    if (!ctx->has_last_diag) return LBM_ERR_STATE;
+    if (int rc = set_device(ctx)) return rc;
+    poll_diag(ctx, true);
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    fill_diag(ctx->hres[1], ctx->last_diag_step, out);
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx *ctx, double *f, double *g, double *S_prev, int on_device)
+{
+    if (!ctx) return LBM_ERR_INVALID_ARG;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    const size_t N = (size_t)ctx->N, QN = (size_t)ctx->Q * N;
+    if (on_device) {
+        CK(d2q9_get_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny, ctx->f[ctx->cur],
+                          ctx->g[ctx->cur], ctx->S, f, g, S_prev, ctx->stream));
+        return LBM_OK;
+    }
+    double *tmp = nullptr;
+    CK(cudaMalloc((void **)&tmp, (2 * QN + N) * sizeof(double)));
+    cudaError_t e = d2q9_get_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny,
+                                   ctx->f[ctx->cur], ctx->g[ctx->cur], ctx->S, tmp, tmp + QN,
+                                   tmp + 2 * QN, ctx->stream);
+    if (e == cudaSuccess && f)
+        e = cudaMemcpyAsync(f, tmp, QN * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && g)
+        e = cudaMemcpyAsync(g, tmp + QN, QN * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && S_prev)
+        e = cudaMemcpyAsync(S_prev, tmp + 2 * QN, N * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    CK(e);
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g, const double *S_prev,
+                  long long step, int on_device)
+{
+    if (!ctx || !f || !g || !S_prev || step < 0) return LBM_ERR_INVALID_ARG;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    const size_t N = (size_t)ctx->N, QN = (size_t)ctx->Q * N;
+    const double *fi = f, *gi = g, *si = S_prev;
+    double *tmp = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc((void **)&tmp, (2 * QN + N) * sizeof(double)));
+        cudaError_t e = cudaMemcpyAsync(tmp, f, QN * sizeof(double), cudaMemcpyHostToDevice,
+                                        ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp + QN, g, QN * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp + 2 * QN, S_prev, N * sizeof(double),
+                                cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return fail_cuda(ctx, e);
+        }
+        fi = tmp;
+        gi = tmp + QN;
+        si = tmp + 2 * QN;
+    }
+    cudaError_t e = d2q9_set_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny, ctx->f[0],
+                                   ctx->g[0], ctx->S, fi, gi, si, ctx->stream);
+    if (tmp) {
+        cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+        cudaFree(tmp);
+        if (e == cudaSuccess) e = e2;
+    }
+    CK(e);
+    ctx->cur = 0;
+    ctx->step = step;
+    ctx->initialized = 1;
+    ctx->has_last_diag = 0;
+    return LBM_OK;
+}
+
+namespace {
+struct SaveHeader {
+    char magic[8];
+    int version, lattice, precision, Q;
+    int nx, ny, nz, pad;
+    long long step;
+};
+}  // namespace
+
+int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
+{
+    if (!ctx || !bytes) return LBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)ctx->N, pop = (size_t)ctx->Q * N * ctx->esz;
+    const size_t need = sizeof(SaveHeader) + 2 * pop + N * ctx->esz;
+    if (!buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (*bytes < need) return LBM_ERR_INVALID_ARG;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    SaveHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "WBLBMCK", 8);
+    h.version = 1;
+    h.lattice = ctx->lattice;
+    h.precision = ctx->prm.precision;
+    h.Q = ctx->Q;
+    h.nx = ctx->grid.nx;
+    h.ny = ctx->grid.ny;
+    h.nz = ctx->grid.nz;
+    h.step = ctx->step;
+    char *b = (char *)buf;
+    memcpy(b, &h, sizeof h);
+    b += sizeof h;
+    CK(cudaMemcpyAsync(b, ctx->f[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + pop, ctx->g[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + 2 * pop, ctx->S, N * ctx->esz, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *bytes = need;
+    return LBM_OK;
+}
+
+int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
+{
+    if (!ctx || !buf) return LBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)ctx->N, pop = (size_t)ctx->Q * N * ctx->esz;
+    const size_t need = sizeof(SaveHeader) + 2 * pop + N * ctx->esz;
+    if (bytes < need) return LBM_ERR_INVALID_ARG;
+    SaveHeader h;
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "WBLBMCK", 8) != 0 || h.version != 1 || h.lattice != ctx->lattice ||
+        h.precision != ctx->prm.precision || h.Q != ctx->Q || h.nx != ctx->grid.nx ||
+        h.ny != ctx->grid.ny || h.nz != ctx->grid.nz || h.step < 0)
+        return LBM_ERR_INVALID_ARG;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    const char *b = (const char *)buf + sizeof h;
+    CK(cudaMemcpyAsync(ctx->f[0], b, pop, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->g[0], b + pop, pop, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->S, b + 2 * pop, N * ctx->esz, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->cur = 0;
+    ctx->step = h.step;
+    ctx->initialized = 1;
+    ctx->has_last_diag = 0;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_INVALID_ARG;
+    if (int rc = set_device(ctx)) return rc;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    poll_diag(ctx, true);
+    return take_err(ctx);
+}
+
+long long lbm_time(const lbm_ctx *ctx) { return ctx ? ctx->step : -1; }
+
+int lbm_derived(const lbm_ctx *ctx, double out[4])
+{
+    if (!ctx || !out) return LBM_ERR_INVALID_ARG;
+    out[0] = ctx->kappa;
+    out[1] = ctx->beta;
+    out[2] = ctx->tau_f;
+    out[3] = ctx->alpha;
+    return LBM_OK;
+}
+
+int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value)
+{
+    if (!ctx || field < 0 || field > 1 || i < 0 || i >= ctx->Q || n < 0 || n >= ctx->N)
+        return LBM_ERR_INVALID_ARG;
+    if (!ctx->initialized) return LBM_ERR_STATE;
+    if (int rc = set_device(ctx)) return rc;
+    if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    // the paper's f_i(x) is stored at x - c_i (pull layout)
+    const int nx = ctx->grid.nx, ny = ctx->grid.ny;
+    const int x = (int)(n % nx), y = (int)(n / nx);
+    const int xs = ((x - HCX[i]) % nx + nx) % nx, ys = ((y - HCY[i]) % ny + ny) % ny;
+    const size_t m = (size_t)i * ctx->N + (size_t)ys * nx + xs;
+    char *base = (char *)(field == 0 ? ctx->f[ctx->cur] : ctx->g[ctx->cur]);
+    if (ctx->esz == 8) {
+        CK(cudaMemcpyAsync(base + m * 8, &value, 8, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+        float v = (float)value;
+        CK(cudaMemcpyAsync(base + m * 4, &v, 4, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    free(ctx);
+}
+
+const char *lbm_strerror(int code)
+{
+    switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of memory";
+    case LBM_ERR_CUDA: return "CUDA error (context unusable)";
+    case LBM_ERR_NONFINITE: return "non-finite value in the fields";
+    case LBM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case LBM_ERR_STATE: return "context not initialised";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"
