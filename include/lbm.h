@@ -159,6 +159,35 @@ int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
  * Errors: STATE if none was recorded yet, CUDA. */
 int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out);
 
+/* Allocation-free diagnostics (the paper has no counterpart: this is a
+ * deployment variant of lbm_diagnostics).  For callers that cannot call
+ * cudaMalloc -- code confined to a host framework's memory pool or a
+ * pre-sized arena, or running where the device allocator must not be
+ * touched -- and so can neither create a context nor let the reduction
+ * allocate its scratch.  It runs the same diagnostics pass and reduction as
+ * lbm_diagnostics; the per-CTA partial records live in a fixed file-scope
+ * device array of 16384 records (1 MiB) that every GPU which loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *   grid, lattice, params: the problem as for lbm_create (D2Q9 only).
+ *   f, g: device arrays [Q][N] in the library's storage layout at
+ *     params->precision (the layout of the population payload written by
+ *     lbm_save: the paper's f_i(x,t) stored at node x - c_i); S_prev: device
+ *     array [N] (u.grad(phi) of the previous step).  Read only.
+ *   out: device array of 8 doubles, written asynchronously:
+ *     {sum phi, E, max |u|^2, mu_min, mu_max, budget, nonfinite (1 or 0), 0}.
+ *   cuda_stream: stream of the two launches (NULL = legacy default stream).
+ * The first call on a device looks up the array's device address on that
+ * device (with it current); make that first call before any stream capture.
+ * Every call shares the one array and it keeps the last call's contents
+ * (each record is rewritten before it is read, so nothing needs clearing):
+ * calls that overlap on the GPU, on any stream, race and give wrong results.
+ * Errors: INVALID_ARG (NULL pointer, bad problem, or a grid whose pass needs
+ * more than 16384 CTAs), CUDA. */
+int lbm_diagnostics_noalloc(const lbm_grid *grid, int lattice, const lbm_params *params,
+                            const void *f, const void *g, const void *S_prev, double *out,
+                            void *cuda_stream);
+
 /* Exchange the full state in the paper's convention, FP64: f[Q*N], g[Q*N]
  * hold f_i(x,t), g_i(x,t) (after streaming, before collision) and
  * S_prev[N] holds u.grad(phi) of step t-1.  lbm_set_state also sets the

@@ -29,7 +29,7 @@ LBM_FP64, LBM_FP32 = 0, 1
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_init_phi", "lbm_step", "lbm_moments",
            "lbm_diagnostics", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
            "lbm_save", "lbm_load", "lbm_sync", "lbm_time", "lbm_derived", "lbm_debug_poke",
-           "lbm_destroy", "lbm_strerror")
+           "lbm_destroy", "lbm_strerror", "lbm_diagnostics_noalloc")
 
 
 class lbm_grid(ctypes.Structure):
@@ -96,6 +96,8 @@ def lib(path: str | None = None):
                                  ctypes.c_double]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_diagnostics_noalloc.argtypes = [ctypes.POINTER(lbm_grid), ctypes.c_int,
+                                          ctypes.POINTER(lbm_params), vp, vp, vp, vp, vp]
     L.lbm_strerror.argtypes = [ctypes.c_int]
     L.lbm_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -214,3 +216,13 @@ def lbm_destroy(h):
 
 def lbm_strerror(code):
     return strerror(code)
+
+
+def lbm_diagnostics_noalloc(grid, lattice, params, f, g, S_prev, out, cuda_stream=0):
+    """All buffers are device addresses (ints or CUDA tensors); see lbm.h."""
+    if not isinstance(grid, lbm_grid):
+        gg = tuple(grid) + (1,) * (3 - len(grid))
+        grid = lbm_grid(*gg)
+    return lib().lbm_diagnostics_noalloc(ctypes.byref(grid), int(lattice), ctypes.byref(params),
+                                         addr(f), addr(g), addr(S_prev), addr(out),
+                                         vp(cuda_stream or None))
