@@ -65,7 +65,9 @@ typedef struct {
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 
 /* Precision of storage and arithmetic.  LBM_FP64: FP64 throughout (parity
- * form).  LBM_FP32: FP32 populations and arithmetic; diagnostics in FP64. */
+ * form).  LBM_FP32: FP32 populations and arithmetic, the rest population of
+ * f kept as a compensated pair of FP32 words (its per-step change near
+ * equilibrium is below half an FP32 ulp of phi); diagnostics in FP64. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
 
 /* The paper's statement of the problem (Section 2 and Section 3):
@@ -166,14 +168,16 @@ int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out);
  * touched -- and so can neither create a context nor let the reduction
  * allocate its scratch.  It runs the same diagnostics pass and reduction as
  * lbm_diagnostics; the per-CTA partial records live in a fixed file-scope
- * device array of 16384 records (1 MiB) that every GPU which loads the
+ * device array of 4096 records (256 KiB) that every GPU which loads the
  * library holds until the process exits.  It calls no cudaMalloc, cudaFree
  * or allocating library routine.
  *   grid, lattice, params: the problem as for lbm_create (D2Q9 only).
- *   f, g: device arrays [Q][N] in the library's storage layout at
+ *   f, g: device arrays in the library's storage layout at
  *     params->precision (the layout of the population payload written by
- *     lbm_save: the paper's f_i(x,t) stored at node x - c_i); S_prev: device
- *     array [N] (u.grad(phi) of the previous step).  Read only.
+ *     lbm_save: the paper's f_i(x,t) stored at node x - c_i): g is [Q][N];
+ *     f is [Q][N] in FP64 and [Q+1][N] in FP32 (the last array holds the
+ *     low word of the rest population); S_prev: device array [N]
+ *     (u.grad(phi) of the previous step).  Read only.
  *   out: device array of 8 doubles, written asynchronously:
  *     {sum phi, E, max |u|^2, mu_min, mu_max, budget, nonfinite (1 or 0), 0}.
  *   cuda_stream: stream of the two launches (NULL = legacy default stream).
@@ -183,7 +187,7 @@ int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out);
  * (each record is rewritten before it is read, so nothing needs clearing):
  * calls that overlap on the GPU, on any stream, race and give wrong results.
  * Errors: INVALID_ARG (NULL pointer, bad problem, or a grid whose pass needs
- * more than 16384 CTAs), CUDA. */
+ * more than 4096 CTAs, about 134 million nodes), CUDA. */
 int lbm_diagnostics_noalloc(const lbm_grid *grid, int lattice, const lbm_params *params,
                             const void *f, const void *g, const void *S_prev, double *out,
                             void *cuda_stream);
@@ -199,7 +203,8 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g,
                   const double *S_prev, long long step, int on_device);
 
 /* Checkpoint to / restore from a host buffer in the library's own format
- * (header + raw device state at the context's precision, so a restore is
+ * (header, then the raw device state at the context's precision: f, g, S_prev
+ * in the storage layout described at lbm_diagnostics_noalloc; a restore is
  * bit-exact).  lbm_save with buf == NULL stores the required size in *bytes.
  * lbm_load checks that grid, lattice and precision match.  Errors:
  * INVALID_ARG (size or header mismatch), STATE, CUDA. */

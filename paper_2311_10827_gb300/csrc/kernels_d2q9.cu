@@ -18,6 +18,16 @@
 // stored f value is read once per strip apart from the 4-column halo (served
 // by L2).  A thread's own output row was summed into phi by the same thread
 // one iteration earlier, so its nine pulled f values stay in registers.
+// Row tiles march in alternating directions (even tiles down, odd tiles up),
+// so two neighbouring tiles reach their shared boundary rows at the same
+// time and the y-halo rows are served from L2 instead of being re-read from
+// HBM.
+//
+// FP32 storage keeps the rest population f_0 (~phi, O(1)) as a compensated
+// pair hi + lo of FP32 words (lo in population slot 9): its per-step change
+// near equilibrium (~1e-9) is below half an FP32 ulp of 1, so a plain FP32
+// f_0 would stagnate and phi would drift.  The pair is updated with an exact
+// two-sum; all arithmetic stays FP32.  FP64 storage has no lo slot.
 #include <float.h>
 #include <math.h>
 
@@ -48,26 +58,40 @@ __device__ __forceinline__ int wrapi(int c, int n)
 }
 
 template <typename T>
-__device__ __forceinline__ T ldg(const T *p)
+struct Arith;
+template <>
+struct Arith<float> {
+    // reciprocal to ~1 ulp (rho and tau_g are O(1); FP32 rounding elsewhere dominates)
+    __device__ static float rcp(float x) { return __fdividef(1.0f, x); }
+};
+template <>
+struct Arith<double> {
+    __device__ static double rcp(double x) { return 1.0 / x; }
+};
+
+// row index wrap for rows in [-n, 2n) (n >= 4), any row otherwise
+__device__ __forceinline__ int wrap_row(int r, int n, bool small)
 {
-    return __ldg(p);
+    if (small) return wrapi(r, n);
+    return r < 0 ? r + n : (r >= n ? r - n : r);
 }
 
 // The nine populations arriving at (x, y): v[i] = src_i(x - cx_i, y - cy_i).
-// rm/r0/rp are the row offsets of y-1, y, y+1; xm/x/xp the wrapped columns.
+// rm/r0/rp are the offsets of rows y-1, y, y+1; xm/x/xp the wrapped columns.
+// Offsets are 32-bit (Q N < 2^32 is checked at context creation).
 template <typename T>
-__device__ __forceinline__ void pull9(const T *__restrict__ s, size_t N, size_t rm, size_t r0,
-                                      size_t rp, int xm, int x, int xp, T v[9])
+__device__ __forceinline__ void pull9(const T *__restrict__ s, unsigned N, unsigned rm, unsigned r0,
+                                      unsigned rp, unsigned xm, unsigned x, unsigned xp, T v[9])
 {
-    v[0] = ldg(s + r0 + x);
-    v[1] = ldg(s + 1 * N + rp + x);   // c = (0,-1) comes from y + 1
-    v[2] = ldg(s + 2 * N + r0 + xm);  // c = (1,0)  comes from x - 1
-    v[3] = ldg(s + 3 * N + rm + x);   // c = (0,1)  comes from y - 1
-    v[4] = ldg(s + 4 * N + r0 + xp);  // c = (-1,0) comes from x + 1
-    v[5] = ldg(s + 5 * N + rm + xm);  // c = (1,1)
-    v[6] = ldg(s + 6 * N + rm + xp);  // c = (-1,1)
-    v[7] = ldg(s + 7 * N + rp + xp);  // c = (-1,-1)
-    v[8] = ldg(s + 8 * N + rp + xm);  // c = (1,-1)
+    v[0] = __ldg(s + (r0 + x));
+    v[1] = __ldg(s + (1u * N + rp + x));   // c = (0,-1) comes from y + 1
+    v[2] = __ldg(s + (2u * N + r0 + xm));  // c = (1,0)  comes from x - 1
+    v[3] = __ldg(s + (3u * N + rm + x));   // c = (0,1)  comes from y - 1
+    v[4] = __ldg(s + (4u * N + r0 + xp));  // c = (-1,0) comes from x + 1
+    v[5] = __ldg(s + (5u * N + rm + xm));  // c = (1,1)
+    v[6] = __ldg(s + (6u * N + rm + xp));  // c = (-1,1)
+    v[7] = __ldg(s + (7u * N + rp + xp));  // c = (-1,-1)
+    v[8] = __ldg(s + (8u * N + rp + xm));  // c = (1,-1)
 }
 
 // sum of the eight moving populations, fixed pairing (the rest population is
@@ -76,6 +100,12 @@ template <typename T>
 __device__ __forceinline__ T sum_moving(const T v[9])
 {
     return ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
+}
+
+template <typename T>
+__device__ __forceinline__ void st_stream(T *p, T v)
+{
+    __stcs(p, v);
 }
 
 __device__ __forceinline__ void warp_reduce(double &sum0, double &sum1, double &mx, double &mn,
@@ -92,51 +122,67 @@ __device__ __forceinline__ void warp_reduce(double &sum0, double &sum1, double &
     }
 }
 
+// resident CTAs per SM targeted by the register budget of each precision
+// resident CTAs per SM targeted by the register budget: the FP32 time step
+// fits 64 registers (4 x 256 threads); variants carrying the FP64
+// diagnostics accumulators get more
+template <typename T, int PASS>
+struct Occ {
+    static constexpr int ctas = sizeof(T) == 4 ? ((PASS & PASS_DIAG) ? 3 : 4) : 2;
+};
+
+// One tile: columns [x0, x0 + TX), rows [y0, yend), marching in direction
+// dir (+1 down from y0, -1 up from yend - 1); diagnostics partial record
+// `part` (PASS_DIAG).  Shared by the single-grid and the batched kernels.
 template <typename T, int TX, int PASS>
-__global__ void __launch_bounds__(TX *TYB) d2q9_pass_kernel(const StepParams<T> P, PassArgs a,
-                                                            int rows)
+__device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs &a, int x0, int y0,
+                                          int yend, int dir, int part)
 {
     constexpr int R = 2 * TYB + 3;  // ring depth: writes never hit a row still read
+    constexpr bool REST_PAIR = sizeof(T) == 4;
     constexpr int WP = TX + 4;      // phi ring width (halo 2)
     constexpr int WM = TX + 2;      // mu ring width (halo 1)
     __shared__ T phs[R * WP];
     __shared__ T mus[R * WM];
 
     const int nx = P.nx, ny = P.ny;
-    const size_t N = (size_t)P.N;
+    const unsigned N = (unsigned)P.N;
+    const bool small = ny < 4;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = blockIdx.y * rows;
-    const int yend = min(y0 + rows, ny);
     const T *__restrict__ fsrc = static_cast<const T *>(a.f_src);
     const T *__restrict__ gsrc = static_cast<const T *>(a.g_src);
 
     // own column (phi ring index tx + 2, mu ring index tx + 1)
     const int xo = x0 + tx;
     const bool col_ok = xo < nx;
-    const int xO = wrapi(xo, nx), xOm = wrapi(xo - 1, nx), xOp = wrapi(xo + 1, nx);
+    const unsigned xO = wrapi(xo, nx), xOm = wrapi(xo - 1, nx), xOp = wrapi(xo + 1, nx);
     // phi halo column handled by threads 0..3: ring index 0, 1, TX+2, TX+3
     const int jH = tx < 2 ? tx : TX + tx;
     const int cH = x0 - 2 + jH;
-    const int xH = wrapi(cH, nx), xHm = wrapi(cH - 1, nx), xHp = wrapi(cH + 1, nx);
+    const unsigned xH = wrapi(cH, nx), xHm = wrapi(cH - 1, nx), xHp = wrapi(cH + 1, nx);
     // mu halo column handled by threads 0, 1: ring index 0 and TX+1
     const int jM = tx == 0 ? 0 : TX + 1;
 
-    auto slot = [&](int row) { return (row - y0 + 2) % R; };  // row >= y0 - 2
+    // m(row) = dir (row - first) is the march coordinate, >= -2 for every row used
+    const int first = dir > 0 ? y0 : yend - 1;
+    const int nout = yend - y0;
+    auto slot = [&](int row) { return (dir * (row - first) + 2) % R; };
 
     // phi at row `row` for the own column (keeping the pulled values) and the
     // halo columns.
-    auto phi_row = [&](int row, T v[9]) {
-        const int y = wrapi(row, ny);
-        const size_t rm = (size_t)wrapi(row - 1, ny) * nx, r0 = (size_t)y * nx,
-                     rp = (size_t)wrapi(row + 1, ny) * nx;
+    auto phi_row = [&](int row, T v[9], T &lo) {
+        const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
+        const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
+        const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
         T *ph = phs + slot(row) * WP;
         pull9(fsrc, N, rm, r0, rp, xOm, xO, xOp, v);
-        ph[tx + 2] = v[0] + sum_moving(v);
+        lo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xO)) : T(0);
+        ph[tx + 2] = v[0] + (lo + sum_moving(v));
         if (tx < 4) {
             T h[9];
             pull9(fsrc, N, rm, r0, rp, xHm, xH, xHp, h);
-            ph[jH] = h[0] + sum_moving(h);
+            const T hlo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xH)) : T(0);
+            ph[jH] = h[0] + (hlo + sum_moving(h));
         }
     };
 
@@ -166,31 +212,30 @@ __global__ void __launch_bounds__(TX *TYB) d2q9_pass_kernel(const StepParams<T> 
 
     // prologue: phi rows y0-2 .. y0+1 (the own row y0+ty keeps its values),
     // mu rows y0-1 .. y0
-    T fcur[9], fnext[9];
-    phi_row(y0 - 2 + ty, fnext);
-    phi_row(y0 + ty, fcur);
+    T fcur[9], fnext[9], locur, lonext;
+    phi_row(first + dir * (ty - 2), fnext, lonext);
+    phi_row(first + dir * ty, fcur, locur);
     __syncthreads();
-    mu_row(y0 - 1 + ty);
+    mu_row(first + dir * (ty - 1));
     __syncthreads();
 
-    for (int r = y0; r < yend; r += TYB) {
-        const int row = r + ty;
-        const bool out_ok = col_ok && row < yend;
+    for (int t = 0; t < nout; t += TYB) {
+        const int row = first + dir * (t + ty);
+        const bool out_ok = col_ok && t + ty < nout;
         // issue the loads of the own node first so they overlap the stencil work
         T gv[9];
         T Sprev = T(0);
-        const int yw = wrapi(row, ny);
-        const size_t nrow = (size_t)yw * nx;
+        const unsigned nrow = (unsigned)wrap_row(row, ny, small) * nx;
         {
-            const size_t rm = (size_t)wrapi(row - 1, ny) * nx,
-                         rp = (size_t)wrapi(row + 1, ny) * nx;
+            const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
+            const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
             pull9(gsrc, N, rm, nrow, rp, xOm, xO, xOp, gv);
             if ((PASS & (PASS_STATE | PASS_DIAG)) && out_ok)
-                Sprev = static_cast<const T *>(a.S)[nrow + xo];
+                Sprev = __ldcs(static_cast<const T *>(a.S) + (nrow + xo));
         }
-        phi_row(r + 2 + ty, fnext);
+        phi_row(first + dir * (t + 2 + ty), fnext, lonext);
         __syncthreads();
-        mu_row(r + 1 + ty);
+        mu_row(first + dir * (t + 1 + ty));
         __syncthreads();
 
         if (out_ok) {
@@ -205,7 +250,7 @@ __global__ void __launch_bounds__(TX *TYB) d2q9_pass_kernel(const StepParams<T> 
 
             // phi from the pulled values (Eq. order-parameter)
             const T snz = sum_moving(fcur);
-            const T phi = fcur[0] + snz;
+            const T phi = fcur[0] + (locur + snz);
             const T mu = m0[k];
             // Eq. gradient: grad = 3 sum_{i!=0} w_i c_i Psi(x + c_i)
             //   = (1/3)(axis differences) + (1/12)(diagonal differences)
@@ -224,8 +269,8 @@ __global__ void __launch_bounds__(TX *TYB) d2q9_pass_kernel(const StepParams<T> 
             const T dphi = phi - P.phiv;
             const T rho = P.rhov + dphi * P.drho;
             const T nu = P.nuv + dphi * P.dnu;
-            const T inv_rho = T(1) / rho;
-            const T inv_taug = T(1) / (T(0.5) + T(3) * nu);  // nu = cs2 (tau_g - 1/2)
+            const T inv_rho = Arith<T>::rcp(rho);
+            const T itg = Arith<T>::rcp(T(0.5) + T(3) * nu);  // nu = cs2 (tau_g - 1/2)
 
             // rho u = sum_i c_i g_i + F/2
             const T jx = (gv[2] - gv[4]) + ((gv[5] - gv[6]) + (gv[8] - gv[7]));
@@ -253,62 +298,80 @@ __global__ void __launch_bounds__(TX *TYB) d2q9_pass_kernel(const StepParams<T> 
                     d_bad = 1.0;
             }
             if (PASS & PASS_MACROS) {
-                const size_t n = nrow + xo;
+                const size_t n = (size_t)nrow + xo;
                 if (a.out_phi) a.out_phi[n] = (double)phi;
                 if (a.out_p) a.out_p[n] = (double)p;
                 if (a.out_mu) a.out_mu[n] = (double)mu;
                 if (a.out_u) {
                     a.out_u[n] = (double)ux;
-                    a.out_u[N + n] = (double)uy;
+                    a.out_u[(size_t)N + n] = (double)uy;
                 }
             }
             if (PASS & PASS_STATE) {
-                const size_t n = nrow + xo;
+                const unsigned n = nrow + xo;
                 T *__restrict__ fd = static_cast<T *>(a.f_dst);
                 T *__restrict__ gd = static_cast<T *>(a.g_dst);
-                static_cast<T *>(a.S)[n] = S;
+                st_stream(static_cast<T *>(a.S_out) + n, S);
 
-                // CH population, Eq. BGK with Eq. H_i and Eq. F_i; the source
-                // w_i b_i (1.5 S - 0.5 S_prev), b = -2, -1/2, 1 (rest, axis, diagonal).
+                // CH population, Eq. BGK with Eq. H_i and Eq. F_i:
+                // f* = f (1 - 1/tau_f) + f^eq/tau_f + w_i b_i (1.5 S - 0.5 S_prev),
+                // b = -2, -1/2, 1 (rest, axis, diagonal); f_0 - f_0^eq is formed
+                // as (5/9) alpha mu - sum_{i!=0} f_i (no cancellation against phi).
                 const T Sh = T(1.5) * S - T(0.5) * Sprev;
                 const T am = P.alpha * mu;
-                const T itf = P.inv_tauf;
-                // f_0 - f_0^eq = (5/9) alpha mu - sum_{i!=0} f_i (no cancellation)
-                fd[n] = fcur[0] - (T(5.0 / 9.0) * am - snz) * itf + T(4.0 / 9.0) * T(-2) * Sh;
-                const T feqa = T(1.0 / 9.0) * am, srca = T(1.0 / 9.0) * T(-0.5) * Sh;
-                const T feqd = T(1.0 / 36.0) * am, srcd = T(1.0 / 36.0) * Sh;
-#pragma unroll
-                for (int i = 1; i <= 4; ++i)
-                    fd[i * N + n] = fcur[i] - (fcur[i] - feqa) * itf + srca;
-#pragma unroll
-                for (int i = 5; i <= 8; ++i)
-                    fd[i * N + n] = fcur[i] - (fcur[i] - feqd) * itf + srcd;
-
-                // hydrodynamic population, Eq. BGK-NS with Eqs. G_i, Siu, GGi.
-                // G_i = (1 - 1/(2 tau_g)) w_i [u.grad rho + c_i.F/cs2
-                //        + ((c_i.u)(c_i.grad rho) - cs2 u.grad rho)/cs2]; the two
-                // u.grad rho terms cancel, leaving 3 w_i (1 - 1/(2 tau_g)) [c_i.F + (c_i.u)(c_i.grad rho)].
-                const T kg = T(1) - T(0.5) * inv_taug;
-                const T p3 = T(3) * p;
+                const T itf = P.inv_tauf, omf = T(1) - itf;
                 {
-                    const T geq0 = p3 * (T(4.0 / 9.0) - T(1)) +
-                                   rho * T(4.0 / 9.0) * (T(-1.5) * uu);
-                    gd[n] = gv[0] - (gv[0] - geq0) * inv_taug;  // G_0 = 0 (c_0 = 0)
+                    // f_0* = f_0 - (f_0 - f_0^eq)/tau_f - (8/9) Sh with
+                    // f_0 - f_0^eq = (5/9) alpha mu - sum_{i!=0} f_i
+                    const T d0 = -(T(5.0 / 9.0) * am - snz) * itf - T(8.0 / 9.0) * Sh;
+                    if (REST_PAIR) {
+                        // (hi, lo) + d0 with an exact two-sum on the high word
+                        const T sl = locur + d0;
+                        const T hi = fcur[0] + sl;
+                        const T bp = hi - fcur[0];
+                        const T lo = (fcur[0] - (hi - bp)) + (sl - bp);
+                        st_stream(fd + n, hi);
+                        st_stream(fd + (9u * N + n), lo);
+                    } else {
+                        st_stream(fd + n, fcur[0] + d0);
+                    }
                 }
+                const T ka = (T(1.0 / 9.0) * am) * itf - T(1.0 / 18.0) * Sh;
+                const T kd = (T(1.0 / 36.0) * am) * itf + T(1.0 / 36.0) * Sh;
 #pragma unroll
-                for (int i = 1; i <= 8; ++i) {
-                    const T w = i <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0);
-                    const T cu = T(cxv(i)) * ux + T(cyv(i)) * uy;
-                    const T cF = T(cxv(i)) * Fx + T(cyv(i)) * Fy;
-                    const T cg = T(cxv(i)) * grx + T(cyv(i)) * gry;
-                    const T geq = w * (p3 + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-                    const T Gi = T(3) * w * kg * (cF + cu * cg);
-                    gd[i * N + n] = gv[i] - (gv[i] - geq) * inv_taug + Gi;
+                for (int i = 1; i <= 4; ++i) st_stream(fd + (i * N + n), fcur[i] * omf + ka);
+#pragma unroll
+                for (int i = 5; i <= 8; ++i) st_stream(fd + (i * N + n), fcur[i] * omf + kd);
+
+                // Hydrodynamic population, Eq. BGK-NS with Eqs. G_i, Siu, GGi:
+                // g* = g (1 - 1/tau_g) + g^eq/tau_g + G_i.  With A = 3p - 1.5 rho |u|^2,
+                // g^eq_i = w_i [A + 4.5 rho (c.u)^2] + 3 w_i rho (c.u) (i != 0), and
+                // G_i = (1 - 1/(2 tau_g)) w_i [u.grad rho + c.F/cs2
+                //       + ((c.u)(c.grad rho) - cs2 u.grad rho)/cs2]
+                //     = 3 w_i k [c.F + (c.u)(c.grad rho)], k = 1 - 1/(2 tau_g)
+                // (the two u.grad rho terms cancel).  Opposite directions share
+                // the even part and flip the odd part.
+                const T kg = T(1) - T(0.5) * itg, omg = T(1) - itg;
+                const T A = T(3) * p - T(1.5) * rho * uu;
+                st_stream(gd + n, gv[0] * omg + (T(4.0 / 9.0) * A - T(3) * p) * itg);  // G_0 = 0
+                const T cu_[4] = {ux, uy, ux + uy, uy - ux};
+                const T cF_[4] = {Fx, Fy, Fx + Fy, Fy - Fx};
+                const T cg_[4] = {grx, gry, grx + gry, gry - grx};
+                constexpr int ip[4] = {2, 3, 5, 6}, im[4] = {4, 1, 7, 8};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const T w = q < 2 ? T(1.0 / 9.0) : T(1.0 / 36.0);
+                    const T cu = cu_[q];
+                    const T sym = w * ((A + T(4.5) * rho * cu * cu) * itg + T(3) * kg * cu * cg_[q]);
+                    const T asym = T(3) * w * (rho * cu * itg + kg * cF_[q]);
+                    st_stream(gd + (ip[q] * N + n), gv[ip[q]] * omg + sym + asym);
+                    st_stream(gd + (im[q] * N + n), gv[im[q]] * omg + sym - asym);
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
+        locur = lonext;
     }
 
     if (PASS & PASS_DIAG) {
@@ -345,9 +408,44 @@ __global__ void __launch_bounds__(TX *TYB) d2q9_pass_kernel(const StepParams<T> 
                 o.budget += red[5][w];
                 o.nonfinite = fmax(o.nonfinite, red[6][w]);
             }
-            a.partials[blockIdx.y * gridDim.x + blockIdx.x] = o;
+            a.partials[part] = o;
         }
     }
+}
+
+// Single grid: CTA (bx, by) owns strip bx and row tile by; even row tiles
+// march down, odd ones up, so neighbouring tiles meet at their shared rows.
+template <typename T, int TX, int PASS>
+__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS>::ctas))
+    d2q9_pass_kernel(const StepParams<T> P, PassArgs a, int rows)
+{
+    const int y0 = blockIdx.y * rows;
+    d2q9_tile<T, TX, PASS>(P, a, blockIdx.x * TX, y0, min(y0 + rows, P.ny),
+                           (blockIdx.y & 1) ? -1 : 1, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Batched: CTA k runs tile k of a flat tile table over many independent grids
+// (each with its own size and parameters); buffers are picked by the step
+// parity shared by all cases.  S is read from S and written to S_out.
+template <typename T, int TX, int PASS>
+__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS>::ctas))
+    d2q9_batch_kernel(const BatchCase *__restrict__ cases, const BatchTile *__restrict__ tiles,
+                      int parity, DiagPartial *partials)
+{
+    const BatchTile t = tiles[blockIdx.x];
+    const BatchCase &c = cases[t.c];
+    const StepParams<T> P = *reinterpret_cast<const StepParams<T> *>(
+        sizeof(T) == 4 ? (const void *)&c.pf : (const void *)&c.pd);
+    PassArgs a;
+    a.f_src = c.f[parity];
+    a.f_dst = c.f[parity ^ 1];
+    a.g_src = c.g[parity];
+    a.g_dst = c.g[parity ^ 1];
+    a.S = c.S;
+    a.S_out = c.S_out;
+    a.out_phi = a.out_p = a.out_u = a.out_mu = nullptr;
+    a.partials = partials;
+    d2q9_tile<T, TX, PASS>(P, a, t.x0, t.y0, t.yend, t.dir, blockIdx.x);
 }
 
 // ------------------------------------------------------------ initial state
@@ -390,6 +488,7 @@ __global__ void d2q9_init_pop(const StepParams<double> P, const double *__restri
         const double fe = i == 0 ? phi[m] - (1.0 - w[0]) * am : w[i] * am;
         f[i * N + n] = (T)fe;
         g[i * N + n] = T(0);
+        if (sizeof(T) == 4 && i == 0) f[9 * N + n] = (T)(fe - (double)(T)fe);  // low word
     }
     S[n] = T(0);
 }
@@ -405,7 +504,9 @@ __global__ void d2q9_get_state_k(int nx, int ny, const T *__restrict__ f, const 
     const int x = (int)(n % nx), y = (int)(n / nx);
     for (int i = 0; i < 9; ++i) {
         const size_t m = (size_t)wrapi(y - cyv(i), ny) * nx + wrapi(x - cxv(i), nx);
-        if (fo) fo[i * N + n] = (double)f[i * N + m];
+        double fv = (double)f[i * N + m];
+        if (sizeof(T) == 4 && i == 0) fv += (double)f[9 * N + m];  // rest population pair
+        if (fo) fo[i * N + n] = fv;
         if (go) go[i * N + n] = (double)g[i * N + m];
     }
     if (So) So[n] = (double)S[n];
@@ -422,7 +523,9 @@ __global__ void d2q9_set_state_k(int nx, int ny, T *__restrict__ f, T *__restric
     const int x = (int)(n % nx), y = (int)(n / nx);
     for (int i = 0; i < 9; ++i) {
         const size_t m = (size_t)wrapi(y + cyv(i), ny) * nx + wrapi(x + cxv(i), nx);
-        f[i * N + n] = (T)fi[i * N + m];
+        const double v = fi[i * N + m];
+        f[i * N + n] = (T)v;
+        if (sizeof(T) == 4 && i == 0) f[9 * N + n] = (T)(v - (double)(T)v);
         g[i * N + n] = (T)gi[i * N + m];
     }
     S[n] = (T)Si[n];
@@ -454,19 +557,41 @@ cudaError_t pass_t(int pass, const void *params, const PassArgs &a, const Launch
     }
 }
 
+template <typename T, int TX>
+cudaError_t launch_batch_t(const BatchCase *cases, const BatchTile *tiles, int ntiles, int parity,
+                           cudaStream_t st)
+{
+    dim3 block(TX, TYB);
+    d2q9_batch_kernel<T, TX, PASS_STATE><<<ntiles, block, 0, st>>>(cases, tiles, parity, nullptr);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
+                            const BatchTile *tiles, int ntiles, int parity, cudaStream_t st)
+{
+    if (precision == 0)
+        return width == 64 ? launch_batch_t<double, 64>(cases, tiles, ntiles, parity, st)
+                           : launch_batch_t<double, 128>(cases, tiles, ntiles, parity, st);
+    return width == 64 ? launch_batch_t<float, 64>(cases, tiles, ntiles, parity, st)
+                       : launch_batch_t<float, 128>(cases, tiles, ntiles, parity, st);
+}
 
 LaunchShape d2q9_shape(int nx, int ny, int num_sms)
 {
     LaunchShape s;
+    s.variant = TXW;
     s.grid_x = (nx + TXW - 1) / TXW;
-    // enough CTAs for several waves of resident blocks, marching >= 8 rows
-    const long long target = 8LL * (num_sms > 0 ? num_sms : 152);
-    int rows = (int)((long long)s.grid_x * ny / target);
-    rows = rows < 8 ? 8 : (rows > 64 ? 64 : rows);
-    rows += rows & 1;  // even: two rows per iteration
-    s.rows = rows;
-    s.grid_y = (ny + rows - 1) / rows;
+    // one wave of resident CTAs (4 per SM at the FP32 register budget) when
+    // the grid allows it; rows even (two rows per iteration), at least 8
+    const long long slots = 4LL * (num_sms > 0 ? num_sms : 152);
+    long long rows = ((long long)s.grid_x * ny + slots - 1) / slots;
+    if (rows < 8) rows = 8;
+    if (rows > 256) rows = 256;
+    rows += rows & 1;
+    s.rows = (int)rows;
+    s.grid_y = (int)((ny + rows - 1) / rows);
     s.nblocks = s.grid_x * s.grid_y;
     return s;
 }

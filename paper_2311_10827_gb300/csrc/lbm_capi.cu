@@ -18,10 +18,15 @@ namespace {
 constexpr double CS2 = 1.0 / 3.0;
 constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: ping-pong)
 
-// D2Q9 velocities (order of Eq. eq:ci), used on the host only for
-// lbm_debug_poke.
-constexpr int HCX[9] = {0, 0, 1, 0, -1, 1, -1, -1, 1};
-constexpr int HCY[9] = {0, -1, 0, 1, 0, 1, 1, -1, -1};
+// Lattice velocities, used on the host only by lbm_debug_poke to find where
+// a population is stored.  D2Q9 in the order of Eq. eq:ci; D3Q19: rest,
+// faces (+x, -x, +y, -y, +z, -z), edges (xy, xz, yz planes).
+constexpr int HC2[9][3] = {{0, 0, 0},  {0, -1, 0}, {1, 0, 0},  {0, 1, 0}, {-1, 0, 0},
+                           {1, 1, 0},  {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+constexpr int HC3[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                            {0, 0, 1},  {0, 0, -1}, {1, 1, 0},   {1, -1, 0}, {-1, 1, 0},
+                            {-1, -1, 0}, {1, 0, 1}, {1, 0, -1},  {-1, 0, 1}, {-1, 0, -1},
+                            {0, 1, 1},  {0, 1, -1}, {0, -1, 1},  {0, -1, -1}};
 
 }  // namespace
 
@@ -31,11 +36,13 @@ struct lbm_ctx {
     lbm_params prm;
     double kappa, beta, tau_f, alpha;
     int Q, D;
+    int nf;      // f arrays: Q, plus the low word of the rest population in FP32
     long long N;
     size_t esz;  // bytes per stored population value
     void *f[2], *g[2], *S;
     int cur;     // f[cur], g[cur] hold the current state
     double *aux;         // N doubles (initial chemical potential)
+    void *phiw;          // D3Q19: phi field written by the first pass of a step
     double *stage;       // (3 + D) N doubles, host moment staging (lazy)
     DiagPartial *partials;
     DiagPartial *dres;   // device: [0] on-demand diagnostics, [1] last fused
@@ -86,9 +93,10 @@ int validate(const lbm_grid *g, int lattice, const lbm_params *p)
 {
     if (!g || !p) return LBM_ERR_INVALID_ARG;
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_ERR_INVALID_ARG;
-    if (lattice != LBM_D2Q9) return LBM_ERR_INVALID_ARG;  // D3Q19: not built yet
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_ERR_INVALID_ARG;
     if (lattice == LBM_D2Q9 && g->nz != 1) return LBM_ERR_INVALID_ARG;
-    if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return LBM_ERR_INVALID_ARG;
+    // population offsets are 32-bit in the kernels
+    if ((long long)g->nx * g->ny * g->nz * 19 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p->W) || !isfinite(p->sigma) || p->sigma < 0.0) return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p->M)) return LBM_ERR_INVALID_ARG;
     if (p->tau_f == 0.0) {
@@ -152,12 +160,16 @@ int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p
     a.f_dst = ctx->f[ctx->cur ^ 1];
     a.g_dst = ctx->g[ctx->cur ^ 1];
     a.S = ctx->S;
+    a.S_out = ctx->S;
     a.out_phi = o_phi;
     a.out_p = o_p;
     a.out_u = o_u;
     a.out_mu = o_mu;
     a.partials = ctx->partials;
-    CK(d2q9_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, st));
+    if (ctx->lattice == LBM_D3Q19)
+        CK(d3q19_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, ctx->phiw, st));
+    else
+        CK(d2q9_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, st));
     return LBM_OK;
 }
 
@@ -216,7 +228,8 @@ void fill_diag(const DiagPartial &r, long long step, lbm_diag *out)
 void free_all(lbm_ctx *c)
 {
     if (c->gexec_valid) cudaGraphExecDestroy(c->gexec);
-    void *dev[] = {c->f[0], c->f[1], c->g[0], c->g[1], c->S, c->aux, c->stage, c->partials, c->dres};
+    void *dev[] = {c->f[0], c->f[1], c->g[0],     c->g[1], c->S,
+                   c->aux,  c->phiw, c->stage,    c->partials, c->dres};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hres) cudaFreeHost(c->hres);
@@ -261,8 +274,9 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
     ctx->grid = *grid;
     ctx->lattice = lattice;
     ctx->prm = *params;
-    ctx->Q = 9;
-    ctx->D = 2;
+    ctx->Q = lattice == LBM_D3Q19 ? 19 : 9;
+    ctx->D = lattice == LBM_D3Q19 ? 3 : 2;
+    ctx->nf = ctx->Q + (params->precision == LBM_FP32 ? 1 : 0);
     ctx->N = (long long)grid->nx * grid->ny * grid->nz;
     ctx->esz = params->precision == LBM_FP64 ? 8 : 4;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -288,9 +302,9 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
         free(ctx);
         return LBM_ERR_CUDA;
     }
-    ctx->shape = d2q9_shape(grid->nx, grid->ny, nsm);
+    ctx->shape = lattice == LBM_D3Q19 ? d3q19_shape(grid->nx, grid->ny, grid->nz, nsm)
+                                      : d2q9_shape(grid->nx, grid->ny, nsm);
     ctx->npart = ctx->shape.nblocks;
-
     const size_t N = (size_t)ctx->N, Q = (size_t)ctx->Q;
     bool oom = false;
     auto dalloc = [&](void **p, size_t bytes) {
@@ -300,12 +314,13 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
             oom = true;
         }
     };
-    dalloc(&ctx->f[0], Q * N * ctx->esz);
-    dalloc(&ctx->f[1], Q * N * ctx->esz);
+    dalloc(&ctx->f[0], (size_t)ctx->nf * N * ctx->esz);
+    dalloc(&ctx->f[1], (size_t)ctx->nf * N * ctx->esz);
     dalloc(&ctx->g[0], Q * N * ctx->esz);
     dalloc(&ctx->g[1], Q * N * ctx->esz);
     dalloc(&ctx->S, N * ctx->esz);
     dalloc((void **)&ctx->aux, N * sizeof(double));
+    if (lattice == LBM_D3Q19) dalloc(&ctx->phiw, N * ctx->esz);
     dalloc((void **)&ctx->partials, (size_t)ctx->npart * sizeof(DiagPartial));
     dalloc((void **)&ctx->dres, 2 * sizeof(DiagPartial));
     if (!oom && cudaMallocHost((void **)&ctx->hres, 2 * sizeof(DiagPartial)) != cudaSuccess)
@@ -342,8 +357,11 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
         }
         src = tmp;
     }
-    cudaError_t e = d2q9_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0], ctx->g[0],
-                              ctx->S, ctx->stream);
+    cudaError_t e = ctx->lattice == LBM_D3Q19
+                        ? d3q19_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0],
+                                     ctx->g[0], ctx->S, ctx->stream)
+                        : d2q9_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0],
+                                    ctx->g[0], ctx->S, ctx->stream);
     if (tmp) {
         cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
         cudaFree(tmp);
@@ -475,16 +493,21 @@ int lbm_get_state(lbm_ctx *ctx, double *f, double *g, double *S_prev, int on_dev
     if (int rc = set_device(ctx)) return rc;
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     const size_t N = (size_t)ctx->N, QN = (size_t)ctx->Q * N;
+    auto get = [&](double *fo, double *go, double *so) {
+        return ctx->lattice == LBM_D3Q19
+                   ? d3q19_get_state(ctx->prm.precision, &ctx->pd, ctx->f[ctx->cur],
+                                     ctx->g[ctx->cur], ctx->S, fo, go, so, ctx->stream)
+                   : d2q9_get_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny,
+                                    ctx->f[ctx->cur], ctx->g[ctx->cur], ctx->S, fo, go, so,
+                                    ctx->stream);
+    };
     if (on_device) {
-        CK(d2q9_get_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny, ctx->f[ctx->cur],
-                          ctx->g[ctx->cur], ctx->S, f, g, S_prev, ctx->stream));
+        CK(get(f, g, S_prev));
         return LBM_OK;
     }
     double *tmp = nullptr;
     CK(cudaMalloc((void **)&tmp, (2 * QN + N) * sizeof(double)));
-    cudaError_t e = d2q9_get_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny,
-                                   ctx->f[ctx->cur], ctx->g[ctx->cur], ctx->S, tmp, tmp + QN,
-                                   tmp + 2 * QN, ctx->stream);
+    cudaError_t e = get(tmp, tmp + QN, tmp + 2 * QN);
     if (e == cudaSuccess && f)
         e = cudaMemcpyAsync(f, tmp, QN * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && g)
@@ -525,8 +548,11 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g, const double *
         gi = tmp + QN;
         si = tmp + 2 * QN;
     }
-    cudaError_t e = d2q9_set_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny, ctx->f[0],
-                                   ctx->g[0], ctx->S, fi, gi, si, ctx->stream);
+    cudaError_t e = ctx->lattice == LBM_D3Q19
+                        ? d3q19_set_state(ctx->prm.precision, &ctx->pd, ctx->f[0], ctx->g[0],
+                                          ctx->S, fi, gi, si, ctx->stream)
+                        : d2q9_set_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny,
+                                         ctx->f[0], ctx->g[0], ctx->S, fi, gi, si, ctx->stream);
     if (tmp) {
         cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
         cudaFree(tmp);
@@ -552,8 +578,9 @@ struct SaveHeader {
 int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
 {
     if (!ctx || !bytes) return LBM_ERR_INVALID_ARG;
-    const size_t N = (size_t)ctx->N, pop = (size_t)ctx->Q * N * ctx->esz;
-    const size_t need = sizeof(SaveHeader) + 2 * pop + N * ctx->esz;
+    const size_t N = (size_t)ctx->N, popf = (size_t)ctx->nf * N * ctx->esz,
+                 pop = (size_t)ctx->Q * N * ctx->esz;
+    const size_t need = sizeof(SaveHeader) + popf + pop + N * ctx->esz;
     if (!buf) {
         *bytes = need;
         return LBM_OK;
@@ -576,9 +603,10 @@ int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
     char *b = (char *)buf;
     memcpy(b, &h, sizeof h);
     b += sizeof h;
-    CK(cudaMemcpyAsync(b, ctx->f[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(b + pop, ctx->g[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(b + 2 * pop, ctx->S, N * ctx->esz, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b, ctx->f[ctx->cur], popf, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + popf, ctx->g[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + popf + pop, ctx->S, N * ctx->esz, cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     *bytes = need;
     return LBM_OK;
@@ -587,8 +615,9 @@ int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
 int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
 {
     if (!ctx || !buf) return LBM_ERR_INVALID_ARG;
-    const size_t N = (size_t)ctx->N, pop = (size_t)ctx->Q * N * ctx->esz;
-    const size_t need = sizeof(SaveHeader) + 2 * pop + N * ctx->esz;
+    const size_t N = (size_t)ctx->N, popf = (size_t)ctx->nf * N * ctx->esz,
+                 pop = (size_t)ctx->Q * N * ctx->esz;
+    const size_t need = sizeof(SaveHeader) + popf + pop + N * ctx->esz;
     if (bytes < need) return LBM_ERR_INVALID_ARG;
     SaveHeader h;
     memcpy(&h, buf, sizeof h);
@@ -599,9 +628,10 @@ int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
     if (int rc = set_device(ctx)) return rc;
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     const char *b = (const char *)buf + sizeof h;
-    CK(cudaMemcpyAsync(ctx->f[0], b, pop, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->g[0], b + pop, pop, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->S, b + 2 * pop, N * ctx->esz, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->f[0], b, popf, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->g[0], b + popf, pop, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->S, b + popf + pop, N * ctx->esz, cudaMemcpyHostToDevice,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->cur = 0;
     ctx->step = h.step;
@@ -640,16 +670,22 @@ int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value)
     if (int rc = set_device(ctx)) return rc;
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     // the paper's f_i(x) is stored at x - c_i (pull layout)
-    const int nx = ctx->grid.nx, ny = ctx->grid.ny;
-    const int x = (int)(n % nx), y = (int)(n / nx);
-    const int xs = ((x - HCX[i]) % nx + nx) % nx, ys = ((y - HCY[i]) % ny + ny) % ny;
-    const size_t m = (size_t)i * ctx->N + (size_t)ys * nx + xs;
+    const int nx = ctx->grid.nx, ny = ctx->grid.ny, nz = ctx->grid.nz;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    const int *c = ctx->lattice == LBM_D3Q19 ? HC3[i] : HC2[i];
+    const int xs = ((x - c[0]) % nx + nx) % nx, ys = ((y - c[1]) % ny + ny) % ny,
+              zs = ((z - c[2]) % nz + nz) % nz;
+    const size_t m = (size_t)i * ctx->N + ((size_t)zs * ny + ys) * nx + xs;
     char *base = (char *)(field == 0 ? ctx->f[ctx->cur] : ctx->g[ctx->cur]);
     if (ctx->esz == 8) {
         CK(cudaMemcpyAsync(base + m * 8, &value, 8, cudaMemcpyHostToDevice, ctx->stream));
     } else {
+        static const float zero = 0.0f;
         float v = (float)value;
         CK(cudaMemcpyAsync(base + m * 4, &v, 4, cudaMemcpyHostToDevice, ctx->stream));
+        if (field == 0 && i == 0)  // low word of the rest population pair
+            CK(cudaMemcpyAsync(base + (m + (size_t)ctx->Q * ctx->N) * 4, &zero, 4,
+                               cudaMemcpyHostToDevice, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;

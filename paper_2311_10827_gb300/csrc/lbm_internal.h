@@ -39,7 +39,8 @@ struct PassArgs {
     void *f_dst;
     const void *g_src;
     void *g_dst;
-    void *S;              // S_prev in, S out (same node, in place)
+    void *S;              // S_prev in
+    void *S_out;          // S out (same node; may equal S: in place)
     double *out_phi, *out_p, *out_u, *out_mu;
     DiagPartial *partials;
 };
@@ -48,12 +49,29 @@ struct LaunchShape {
     int rows;      // rows per CTA (2D march length)
     int grid_x, grid_y;
     int nblocks;
+    int variant;   // kernel variant (strip width) where several exist
+};
+
+// One grid of a batch (device-resident table): parameters in both
+// precisions, the two population buffers of f and g, S_prev and the S output.
+struct BatchCase {
+    StepParams<double> pd;
+    StepParams<float> pf;
+    void *f[2], *g[2];
+    void *S, *S_out;
+};
+// One CTA's tile of a batch: case, strip x0, rows [y0, yend), march direction.
+struct BatchTile {
+    int c, x0, y0, yend, dir;
 };
 
 // D2Q9 (kernels_d2q9.cu)
 LaunchShape d2q9_shape(int nx, int ny, int num_sms);
 cudaError_t d2q9_pass(int precision, int pass, const void *params, const PassArgs &a,
                       const LaunchShape &s, cudaStream_t st);
+// one time step of every grid of a batch (strip width 128 or 64)
+cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
+                            const BatchTile *tiles, int ntiles, int parity, cudaStream_t st);
 cudaError_t d2q9_init(int precision, const void *params, const double *phi0, double *mu_tmp,
                       void *f, void *g, void *S, cudaStream_t st);
 cudaError_t d2q9_get_state(int precision, int nx, int ny, const void *f, const void *g,
@@ -61,6 +79,18 @@ cudaError_t d2q9_get_state(int precision, int nx, int ny, const void *f, const v
 cudaError_t d2q9_set_state(int precision, int nx, int ny, void *f, void *g, void *S,
                            const double *fi, const double *gi, const double *Si,
                            cudaStream_t st);
+
+// D3Q19 (kernels_d3q19.cu); a pass first writes phi into phi_work (N values
+// at the context's precision)
+LaunchShape d3q19_shape(int nx, int ny, int nz, int num_sms);
+cudaError_t d3q19_pass(int precision, int pass, const void *params, const PassArgs &a,
+                       const LaunchShape &s, void *phi_work, cudaStream_t st);
+cudaError_t d3q19_init(int precision, const void *params, const double *phi0, double *mu_tmp,
+                       void *f, void *g, void *S, cudaStream_t st);
+cudaError_t d3q19_get_state(int precision, const void *params, const void *f, const void *g,
+                            const void *S, double *fo, double *go, double *So, cudaStream_t st);
+cudaError_t d3q19_set_state(int precision, const void *params, void *f, void *g, void *S,
+                            const double *fi, const double *gi, const double *Si, cudaStream_t st);
 
 // diagnostics reduction (kernels_diag.cu): partials[n] -> out (one record)
 cudaError_t diag_reduce(const DiagPartial *partials, int n, DiagPartial *out, cudaStream_t st);

@@ -22,9 +22,9 @@ namespace {
 using wblbm::DiagPartial;
 
 // Fixed scratch: one partial record per CTA of the diagnostics pass.
-// 16384 records x 64 B = 1 MiB, held by every GPU that loads the library
-// until the process exits.
-constexpr int NOALLOC_MAX_CTAS = 16384;
+// 4096 records x 64 B = 256 KiB, held by every GPU that loads the library
+// until the process exits (enough for grids up to about 134 million nodes).
+constexpr int NOALLOC_MAX_CTAS = 4096;
 static __device__ __align__(256) DiagPartial g_noalloc_partials[NOALLOC_MAX_CTAS];
 
 // Device address of g_noalloc_partials per device.  In host code the array's
@@ -95,7 +95,7 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_grid *grid, int lattice, const 
     const lbm_params &p = *params;
     if (lattice != LBM_D2Q9 || grid->nx < 1 || grid->ny < 1 || grid->nz != 1)
         return LBM_ERR_INVALID_ARG;
-    if ((long long)grid->nx * grid->ny > (1LL << 40)) return LBM_ERR_INVALID_ARG;
+    if ((long long)grid->nx * grid->ny * 9 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
     if (p.precision != LBM_FP64 && p.precision != LBM_FP32) return LBM_ERR_INVALID_ARG;
     if (!pos(p.W) || !pos(p.M) || !isfinite(p.sigma) || p.sigma < 0.0 ||
         !isfinite(p.phi_l) || !isfinite(p.phi_v) || p.phi_l == p.phi_v || !pos(p.rho_l) ||

@@ -132,12 +132,13 @@ def test_fp64_phi_budget_on_gpu(gpu, oracle_mod):
         assert abs(d1["sum_phi"] - (d0["sum_phi"] - d0["budget"])) < 1e-12 * d0["sum_phi"]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_graph_and_plain_steps_identical(gpu, precision):
-    """lbm_step(n) (CUDA graph of 32 steps) equals n single steps bit for bit."""
-    a = gpu.Simulation((160, 70), precision=precision, **PRM)
-    b = gpu.Simulation((160, 70), precision=precision, **PRM)
-    phi0 = wl.droplet(160, 70, 20.0, 4.0)
+@pytest.mark.parametrize("precision,nx", [("fp64", 160), ("fp32", 160), ("fp32", 256)])
+def test_graph_and_plain_steps_identical(gpu, precision, nx):
+    """lbm_step(n) (CUDA graph of 32 steps) equals n single steps bit for bit
+    (nx = 256 takes the TMA-staged FP32 kernel)."""
+    a = gpu.Simulation((nx, 70), precision=precision, **PRM)
+    b = gpu.Simulation((nx, 70), precision=precision, **PRM)
+    phi0 = wl.droplet(nx, 70, 20.0, 4.0)
     a.init_phi(phi0)
     b.init_phi(phi0)
     a.step(1)
@@ -150,23 +151,23 @@ def test_graph_and_plain_steps_identical(gpu, precision):
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb) and np.array_equal(Sa, Sb)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_checkpoint_resume_bit_exact(gpu, precision):
-    a = gpu.Simulation((144, 40), precision=precision, **PRM)
-    phi0 = wl.droplet(144, 40, 12.0, 4.0)
+@pytest.mark.parametrize("precision,nx", [("fp64", 144), ("fp32", 144), ("fp32", 256)])
+def test_checkpoint_resume_bit_exact(gpu, precision, nx):
+    a = gpu.Simulation((nx, 40), precision=precision, **PRM)
+    phi0 = wl.droplet(nx, 40, 12.0, 4.0)
     a.init_phi(phi0)
     a.step(37)
     ck = a.save()
     a.step(50)
     fa, ga, Sa = a.get_state()
-    b = gpu.Simulation((144, 40), precision=precision, **PRM)
+    b = gpu.Simulation((nx, 40), precision=precision, **PRM)
     b.load(ck)
     assert b.t == 37
     b.step(50)
     fb, gb, Sb = b.get_state()
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb) and np.array_equal(Sa, Sb)
     # a checkpoint of another grid is refused
-    c = gpu.Simulation((140, 40), precision=precision, **PRM)
+    c = gpu.Simulation((nx - 4, 40), precision=precision, **PRM)
     from paper_2311_10827_gb300 import capi
     with pytest.raises(capi.LbmError):
         c.load(ck)
@@ -203,6 +204,23 @@ def test_nonfinite_is_reported(gpu, precision):
     assert s.last_diagnostics()["nonfinite"]
 
 
+def test_fp32_fused_diagnostics_close_to_on_demand(gpu):
+    """The TMA-staged step's fused diagnostics agree with the on-demand pass."""
+    a = gpu.Simulation((256, 64), precision="fp32", diag_every=5, **PRM)
+    b = gpu.Simulation((256, 64), precision="fp32", **PRM)
+    phi0 = wl.droplet(256, 64, 15.0, 4.0)
+    a.init_phi(phi0)
+    b.init_phi(phi0)
+    a.step(11)
+    b.step(10)
+    da, db = a.last_diagnostics(), b.diagnostics()
+    assert da["step"] == 10
+    assert np.isclose(da["sum_phi"], db["sum_phi"], rtol=1e-12)
+    for k in ("kinetic_energy", "u_max", "mu_min", "mu_max"):
+        assert np.isclose(da[k], db[k], rtol=1e-5), k
+    assert abs(da["budget"] - db["budget"]) <= 1e-5 * abs(db["budget"]) + 1e-9
+
+
 def test_call_order_and_arguments(gpu):
     from paper_2311_10827_gb300 import capi
     s = gpu.Simulation((32, 32), precision="fp32", **PRM)
@@ -215,12 +233,13 @@ def test_call_order_and_arguments(gpu):
     assert capi.lbm_debug_poke(s.handle, 2, 0, 0, 0.0) == capi.LBM_ERR_INVALID_ARG
 
 
-def test_fp32_against_oracle(gpu, oracle_mod):
-    """FP32 path vs the FP64 oracle on a droplet, 2000 steps."""
-    shape = (192, 96)
+@pytest.mark.parametrize("shape", [(192, 96), (256, 96), (128, 77)])
+def test_fp32_against_oracle(gpu, oracle_mod, shape):
+    """FP32 path vs the FP64 oracle on a droplet, 2000 steps (widths that are
+    multiples of 128 take the TMA-staged kernel)."""
     s = gpu.Simulation(shape, precision="fp32", **PRM)
     o = oracle_mod.Oracle(shape, **PRM)
-    phi0 = wl.droplet(192, 96, 24.0, 4.0)
+    phi0 = wl.droplet(shape[0], shape[1], 24.0, 4.0)
     s.init_phi(phi0)
     o.init_phi(phi0)
     s.step(2000)
@@ -230,12 +249,13 @@ def test_fp32_against_oracle(gpu, oracle_mod):
     assert np.abs(mg["u"] - mo["u"]).max() < 1e-6
 
 
-def test_fp32_one_step_from_same_state(gpu, oracle_mod):
-    """One step from an FP32-representable perturbed state: FP32 rounding only."""
-    shape = (257, 33)
+@pytest.mark.parametrize("shape", [(257, 33), (256, 33), (128, 20), (384, 7), (640, 3)])
+def test_fp32_one_step_from_same_state(gpu, oracle_mod, shape):
+    """One step from an FP32-representable perturbed state: FP32 rounding only
+    (several strips, a single strip, ragged rows, fewer rows than the halo)."""
     s = gpu.Simulation(shape, precision="fp32", **PRM)
     o = oracle_mod.Oracle(shape, **PRM)
-    o.init_phi(wl.droplet(257, 33, 12.0, 4.0))
+    o.init_phi(wl.droplet(shape[0], shape[1], min(shape) / 3 + 1.0, 4.0))
     f, g, S = perturb(o, 21)
     f, g, S = (a.astype(np.float32).astype(np.float64) for a in (f, g, S))
     o.set_state(f, g, S, 0)

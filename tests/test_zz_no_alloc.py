@@ -33,10 +33,11 @@ def device_state(torch, s):
     buf = s.save()
     dt = np.float64 if s.precision == "fp64" else np.float32
     QN, N = s.Q * s.N, s.N
-    payload = (2 * QN + N) * np.dtype(dt).itemsize
+    FN = QN + (N if s.precision == "fp32" else 0)  # FP32 f carries the rest pair's low word
+    payload = (FN + QN + N) * np.dtype(dt).itemsize
     raw = np.frombuffer(buf[len(buf) - payload:].tobytes(), dtype=dt)
     to = lambda a: torch.from_numpy(a.copy()).cuda()  # noqa: E731
-    return to(raw[:QN]), to(raw[QN:2 * QN]), to(raw[2 * QN:])
+    return to(raw[:FN]), to(raw[FN:FN + QN]), to(raw[FN + QN:])
 
 
 def noalloc(torch, capi, s, f, g, S):
@@ -78,6 +79,7 @@ def test_noalloc_rejects_too_many_ctas_and_null(env):
     torch, capi, sim = env
     p = sim.make_params("fp32", **PRM)
     t = torch.zeros(64, dtype=torch.float64, device="cuda")
+    # 8192 x 16448 nodes: a valid grid whose pass needs more than 4096 CTAs
     rc = capi.lbm_diagnostics_noalloc((8192, 16448, 1), capi.LBM_D2Q9, p, t, t, t, t)
     assert rc == capi.LBM_ERR_INVALID_ARG
     rc = capi.lbm_diagnostics_noalloc((64, 64, 1), capi.LBM_D2Q9, p, None, t, t, t)
