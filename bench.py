@@ -8,17 +8,18 @@ nu_v = 0.1), D2Q9, FP32; one bench step advances both density-ratio cases
 kernel).  Synthetic input: the tanh droplet of the paper's stationary-droplet
 test (Section 3.2), no dataset involved.
 
+The step is the batched form: one kernel launch advances both grids
+(tile shape from the library's autotuner, steps replayed from a CUDA graph),
+and every --diag-every steps the FP64 diagnostics of both grids are reduced
+and read back.
+
 Metric: MLUPS (million node updates per second, both populations).  `value`
-is device time (CUDA events around every timed step on the launching
-stream), steps back to back: each step's inputs (2 x 79 MB) exceed the
-129 MB L2 and each grid is re-read only after the other grid's pass, so
-reads come from HBM and every kernel pays the write-backs of the one before
-(--l2-flush instead writes and reads a 256 MiB buffer between timed steps,
-outside the events).  `e2e` is wall-clock through the C ABI with host
-buffers: pinned host phi0 uploaded by lbm_init_phi, every step followed by a
-device-to-host read of the run's latest diagnostics record (refreshed by the
-fused diagnostics every --diag-every steps), the final fields read back by
-lbm_moments.
+is device time (CUDA events on the launching stream around the timed
+region), steps back to back: each step reads 2 x 84 MB, more than the 129 MB
+L2, so reads come from HBM and every launch pays the write-backs of the one
+before.  `e2e` is wall-clock through the C ABI with host buffers: pinned host
+phi0 uploaded by lbm_init_phi, the same steps and diagnostics read-backs, the
+final fields of both grids read back by lbm_moments.
 
 Multi-GPU: replicas only (every rank runs its own pair of grids, weak
 scaling; the only collectives are the timing barrier and max).
@@ -45,8 +46,8 @@ RATIOS = (10.0, 100.0)
 # bytes moved per node update: f, g read + write (4 Q s) and S read + write;
 # FP32 also moves the low word of the rest population pair (8 B)
 BYTES_PER_NODE = {"fp32": 160, "fp64": 304}
-L2_FLUSH_BYTES = 256 << 20
 KERNEL_SOURCES = ("paper_2311_10827_gb300/csrc/kernels_d2q9.cu",)
+TRAFFIC_KERNEL = "d2q9_batch_kernel"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_d2q9_fp32_droplet1024.txt")
 
 
@@ -96,28 +97,31 @@ def ncu_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms.  Started
+    before the warm-up (its start-up must not fall in the timed region);
+    summary() keeps the samples time-stamped inside the timed window."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(1.0)
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -126,24 +130,29 @@ class ClockSampler:
                 self.proc.kill()
                 self.out, _ = self.proc.communicate()
 
-    def summary(self):
+    def summary(self, t_start=None, t_end=None):
+        import datetime
         rows = []
         for line in (self.out or "").splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                rows.append((float(f[1]), float(f[2]), f[5:9]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-        if not rows:
+        inside = [r for r in rows if t_start is None or t_start - 0.05 <= r[0] <= t_end + 0.05]
+        if not inside and rows and t_start is not None:  # region shorter than the period
+            inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (t_start + t_end)))]
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[k] for _, _, r in rows for k in range(4)
-                          if r[k].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(r[0] for r in rows),
-                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        reasons = sorted({names[k] for r in inside for k in range(4)
+                          if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": reasons,
+                "samples": len(inside)}
 
 
 def cpu_baseline(steps=None, budget_s=12.0):
@@ -210,107 +219,106 @@ def run_native(args, rank, world, local_rank):
     from paper_2311_10827_gb300 import build as B
     B.build()
     from paper_2311_10827_gb300 import capi
-    from paper_2311_10827_gb300.sim import Simulation
+    from paper_2311_10827_gb300.sim import Batch
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     prec = args.precision
-    sims = [Simulation((NX, NY), precision=prec, stream=stream.cuda_stream,
-                       diag_every=args.diag_every, **params(r)) for r in RATIOS]
-    phi_d = torch.tensor(phi0(), dtype=torch.float64, device=dev)
-    for s in sims:
-        s.init_phi(phi_d)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def l2_flush(i):
-        flush.fill_(float(i))
-        flush.sum()
+    de = args.diag_every
+    cases = [((NX, NY), params(r)) for r in RATIOS]
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    for i in range(args.warmup):
-        if args.l2_flush:
-            l2_flush(i)
-        for s in sims:
-            s.step(1)
-    barrier()
+    def max_over_ranks(x):
+        return max_over_ranks_dist(x, world, dev)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(sims) + 1)]
-           for _ in range(args.steps)]
-    t_first = sims[0].t
+    def chunks(k):
+        out, left = [], k
+        while left > 0:
+            out.append(min(de, left))
+            left -= out[-1]
+        return out
+
+    # ---- device-resident timing: one batched launch per step over both grids
+    batch = Batch(cases, precision=prec, stream=stream.cuda_stream)
+    phi_d = torch.tensor(phi0(), dtype=torch.float64, device=dev)
+    for i in range(len(batch)):
+        batch.case(i).init_phi(phi_d)
+    if args.tile:
+        width, rows = (int(v) for v in args.tile.lower().split("x"))
+        batch.set_shape(width, rows)
+    else:
+        width, rows = batch.tune()
+    plan = chunks(args.steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in plan]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
+        batch.step(args.warmup)
+        barrier()
         t_wall = time.perf_counter()
-        for k in range(args.steps):
-            if args.l2_flush:
-                l2_flush(k)
-            starts[k].record(stream)
-            kev[k][0].record(stream)
-            for j, s in enumerate(sims):
-                s.step(1)
-                kev[k][j + 1].record(stream)
-            ends[k].record(stream)
+        t_start = time.time()
+        t0.record(stream)
+        for (a, b), m in zip(ev, plan):
+            a.record(stream)
+            batch.step(m)
+            b.record(stream)
+            for i in range(len(batch)):  # FP64 diagnostics of both grids (a10)
+                rc, d = capi.lbm_diagnostics(batch.case(i).handle)
+                capi.check(rc)
+                if d.nonfinite:
+                    raise RuntimeError("non-finite fields in the timed run")
+        t1.record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
-    step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
-    # single-kernel durations of plain steps (no fused diagnostics at that step)
-    de = args.diag_every
-    plain = [kev[k][j].elapsed_time(kev[k][j + 1]) for k in range(args.steps)
-             for j in range(len(sims)) if de == 0 or (t_first + k) % de != 0]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    nodes = NX * NY * len(sims)
+        t_end = time.time()
+    total_s = max_over_ranks(t0.elapsed_time(t1) / 1e3)
+    kernel_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps  # per batched launch
+    nodes = NX * NY * len(cases)
     value = nodes * args.steps * world / total_s / 1e6
+    ntiles = batch.shape()[2]
+    batch.close()
 
     # ---- end to end through the C ABI with host buffers
     hphi = torch.tensor(phi0(), dtype=torch.float64).pin_memory()
     hphi_np = hphi.numpy()
-    e2e_steps = args.steps
     outs = [dict(phi=np.empty(NX * NY), p=np.empty(NX * NY), mu=np.empty(NX * NY),
-                 u=np.empty(2 * NX * NY)) for _ in sims]
-    e2e_sims = [Simulation((NX, NY), precision=prec, stream=stream.cuda_stream,
-                           diag_every=args.diag_every, **params(r)) for r in RATIOS]
+                 u=np.empty(2 * NX * NY)) for _ in cases]
+    eb = Batch(cases, precision=prec, stream=stream.cuda_stream)
+    if args.tile:
+        eb.set_shape(width, rows)
     barrier()
-    t0 = time.perf_counter()
-    for s in e2e_sims:
-        capi.check(capi.lbm_init_phi(s.handle, hphi_np, 0))
-    for k in range(e2e_steps):
-        for s in e2e_sims:
-            capi.check(capi.lbm_step(s.handle, 1))
-        for s in e2e_sims:
-            rc, d = capi.lbm_last_diagnostics(s.handle)
+    t_e = time.perf_counter()
+    for i in range(len(eb)):
+        capi.check(capi.lbm_init_phi(eb.case(i).handle, hphi_np, 0))
+    n_diag_reads = 0  # the first lbm_batch_step runs the autotuner (inside the timed region)
+    for m in plan:
+        capi.check(capi.lbm_batch_step(eb.handle, m))
+        for i in range(len(eb)):
+            rc, d = capi.lbm_diagnostics(eb.case(i).handle)  # device -> host read
             capi.check(rc)
-    for s, o in zip(e2e_sims, outs):
-        capi.check(capi.lbm_moments(s.handle, o["phi"], o["p"], o["u"], o["mu"], 0))
+            n_diag_reads += 1
+    for i, o in enumerate(outs):
+        capi.check(capi.lbm_moments(eb.case(i).handle, o["phi"], o["p"], o["u"], o["mu"], 0))
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = nodes * e2e_steps * world / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t_e)
+    eb.close()
+    e2e_value = nodes * args.steps * world / e2e_s / 1e6
     diag_bytes = ctypes_sizeof_diag()
-    h2d = NX * NY * 8 * len(sims) / e2e_steps
-    d2h = diag_bytes * len(sims) + 5 * NX * NY * 8 * len(sims) / e2e_steps
-    for s in e2e_sims:
-        s.close()
+    h2d = NX * NY * 8 * len(cases) / args.steps
+    d2h = (n_diag_reads * diag_bytes + 5 * NX * NY * 8 * len(cases)) / args.steps
 
     if rank != 0:
         return
     peaks, src = measured_peaks()
-    avg_kernel_s = statistics.mean(plain) / 1e3 if plain else None
     bpn = BYTES_PER_NODE[prec]
-    achieved = bpn * NX * NY / avg_kernel_s / 1e9 if avg_kernel_s else None
+    achieved = bpn * nodes / kernel_s / 1e9
     traffic = ncu_traffic() if prec == "fp32" else None
-    n_diag = sum(1 for k in range(args.steps) if de > 0 and (t_first + k) % de == 0)
     line = {
         "metric": "MLUPS (fused f+g step)", "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -319,29 +327,94 @@ def run_native(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": "2D stationary droplet 1024x1024 periodic, R=128, W=4, "
                                "sigma=1e-3, M=0.05, nu_l/nu_v=10, rho_l/rho_v=10 and 100 "
-                               "(one step = both grids)",
+                               "(one step = both grids, one batched launch)",
                    "lattice": "D2Q9", "nodes_per_step": nodes, "diag_every": de,
-                   "l2": ("256 MiB write+read flush between timed steps, outside the events"
-                          if args.l2_flush else
-                          "inputs larger than L2: 2 x 79 MB per step, back to back"),
+                   "tile": {"width": width, "rows": rows, "ctas": ntiles},
+                   "l2": "inputs larger than L2: 2 x 84 MB read per step, back to back",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": traffic, "peak_source": f"{src} copy bandwidth (hbm_gbs)",
-                     "algorithmic_bytes_per_node": bpn,
-                     "kernel_ms": avg_kernel_s * 1e3 if avg_kernel_s else None},
+                     "algorithmic_bytes_per_node": bpn, "kernel_ms": kernel_s * 1e3,
+                     "kernel": "d2q9_batch_kernel (both grids per launch)"},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "how": "lbm_init_phi from pinned host phi0, per step lbm_step + "
-                       "lbm_last_diagnostics (D2H of the latest diagnostics record), final "
-                       "lbm_moments to host; wall clock"},
-        "gpu_launches": args.steps * len(sims) + n_diag * len(sims),
-        "clocks": clk.summary(),
+                "how": "wall clock through the C ABI: lbm_init_phi from pinned host phi0, "
+                       "lbm_batch_step (autotune on the first call) in chunks of diag_every steps each followed "
+                       "by lbm_diagnostics (device-to-host read) of both grids, final "
+                       "lbm_moments of both grids to host"},
+        "gpu_launches": args.steps + 4 * len(plan),
+        "clocks": clk.summary(t_start, t_end),
         "wall_s_timed_region": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+def run_ensemble(args, rank, world, local_rank):
+    """The batched ensemble: 256 stationary droplets, N x N grids with N drawn
+    from U{64..512}, R = U(0.15, 0.35) N, rho_l/rho_v = U(1, 100) (seeds 0..255,
+    workloads.ensemble_case), W = 4, other parameters of the 1024^2 droplet;
+    one batched launch per step."""
+    import torch
+
+    from paper_2311_10827_gb300 import build as B
+    B.build()
+    from paper_2311_10827_gb300 import workloads as wl
+    from paper_2311_10827_gb300.sim import Batch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    base = wl.physical(wl.DROPLET_1024)
+    cases, phis = [], []
+    for seed in range(256):
+        c = wl.ensemble_case(seed)
+        prm = dict(base, rho_l=c["rho_ratio"] * base["rho_v"])
+        cases.append(((c["n"], c["n"]), prm))
+        phis.append(wl.droplet(c["n"], c["n"], c["R"], base["W"]))
+    b = Batch(cases, precision=args.precision, stream=stream.cuda_stream)
+    for i, phi in enumerate(phis):
+        b.case(i).init_phi(phi)
+    width, rows = b.tune()
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = max_over_ranks_dist(e0.elapsed_time(e1) / 1e3, world, dev)
+    nodes = sum(sh[0] * sh[1] for sh, _ in cases)
+    peaks, src = measured_peaks()
+    bpn = BYTES_PER_NODE[args.precision]
+    if rank == 0:
+        v = nodes * args.steps * world / dt / 1e6
+        print(json.dumps({
+            "metric": "MLUPS (fused f+g step)", "value": v, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "batched ensemble: 256 stationary 2D droplets, grids "
+                                   "64^2..512^2, seeds 0..255", "nodes_per_step": nodes,
+                       "tile": {"width": width, "rows": rows, "ctas": b.shape()[2]}},
+            "roofline": {"bound": "hbm", "achieved": bpn * v * 1e6 / 1e9 / world,
+                         "peak": peaks["hbm_gbs"],
+                         "frac": bpn * v * 1e6 / 1e9 / world / peaks["hbm_gbs"], "unit": "GB/s",
+                         "traffic": None, "peak_source": f"{src} copy bandwidth (hbm_gbs)"}}),
+              flush=True)
+    b.close()
+
+
+def max_over_ranks_dist(x, world, device):
+    """Max of a float over the ranks (identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def ctypes_sizeof_diag():
@@ -360,7 +433,10 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--diag-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--l2-flush", action="store_true")
+    ap.add_argument("--tile", default="", help="WxR: fixed batch tile shape instead of the "
+                    "autotuner (profiling commands use the shape the tuner picked)")
+    ap.add_argument("--workload", choices=["droplet1024", "ensemble"], default="droplet1024",
+                    help="droplet1024: the headline line; ensemble: the 256-grid batch")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -376,7 +452,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_native(args, rank, world, local_rank)
+        if args.workload == "ensemble":
+            run_ensemble(args, rank, world, local_rank)
+        else:
+            run_native(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

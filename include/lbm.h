@@ -225,6 +225,87 @@ int lbm_derived(const lbm_ctx *ctx, double out[4]);
  * Errors: STATE, INVALID_ARG, CUDA. */
 int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble (not in the paper: a throughput form of the same step).
+ * Many independent periodic D2Q9 grids, each with its own size and problem
+ * parameters (all at one precision), advance together: every time step is a
+ * single kernel launch over a flat table of tiles that covers all grids, long
+ * runs replay a CUDA graph of such launches, and the tile shape (strip width
+ * 64 or 128 columns, rows per tile) is chosen by an autotuner that times
+ * candidate shapes on the batch's own state.  Each grid is also an ordinary
+ * context (lbm_batch_case) for initialisation, moments, diagnostics, state
+ * exchange and checkpoints; those calls act on that grid only.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* Create ncases contexts (grids[c], params[c]; lattice D2Q9; every
+ * params[c].precision equal; params[c].diag_every is ignored by batch steps)
+ * on the current device, issuing work on cuda_stream.  Errors: INVALID_ARG
+ * (ncases < 1, NULL arrays, a grid or parameter set that lbm_create rejects,
+ * mixed precisions), OOM, CUDA. */
+int lbm_batch_create(int ncases, const lbm_grid *grids, const lbm_params *params,
+                     void *cuda_stream, lbm_batch **out);
+
+/* The context of grid c (owned by the batch; do not destroy it).  Stepping it
+ * with lbm_step desynchronises it from the batch: lbm_batch_step then returns
+ * LBM_ERR_STATE until every grid is re-initialised.  Errors: INVALID_ARG. */
+int lbm_batch_case(lbm_batch *b, int c, lbm_ctx **ctx);
+
+/* Advance every grid by n >= 0 steps (asynchronous).  All grids must be
+ * initialised and at the same time step.  The first call runs the autotuner
+ * unless lbm_batch_tune was called.  Errors: STATE, INVALID_ARG, CUDA. */
+int lbm_batch_step(lbm_batch *b, int n);
+
+/* Time every candidate tile shape on the current state (the state is left
+ * unchanged: candidates write only to scratch) and keep the fastest; report
+ * it in *width and *rows (either may be NULL).  Synchronises.  Errors: STATE
+ * (a grid not initialised), CUDA. */
+int lbm_batch_tune(lbm_batch *b, int *width, int *rows);
+
+/* Current tile shape and number of tiles (CTAs per step). */
+int lbm_batch_shape(const lbm_batch *b, int *width, int *rows, int *ntiles);
+
+/* Use tile shape (width 64 or 128, rows >= 2) without tuning; later
+ * lbm_batch_step calls do not tune.  Errors: INVALID_ARG, OOM, CUDA. */
+int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
+
+/* Release the batch and all its contexts (synchronises first).  NULL-safe. */
+void lbm_batch_destroy(lbm_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Discrete adjoint (not in the paper: the gradient of the discrete map).
+ * For a D2Q9 context, records a run from an initial field phi0 with a
+ * checkpoint of the state every `checkpoint_every` steps (device memory),
+ * then, given dL/dphi of the final state, returns dL/dphi0 and the gradients
+ * with respect to the surface tension and the mobility.  Segments between
+ * checkpoints are recomputed forward on the backward pass; the reverse step
+ * runs in FP64 whatever the context's precision.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_adjoint lbm_adjoint;
+
+/* Attach an adjoint recorder to ctx (D2Q9) for runs of at most max_steps
+ * steps; allocates max_steps / checkpoint_every + 1 checkpoints and one
+ * segment of checkpoint_every states.  Errors: INVALID_ARG (D3Q19 context,
+ * checkpoint_every < 1, max_steps < 1), OOM, CUDA. */
+int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_adjoint **out);
+
+/* lbm_init_phi(phi0) then nsteps (<= max_steps) steps of the context, keeping
+ * the checkpoints.  phi0 is FP64 [N], host (on_device = 0) or device.
+ * Errors: INVALID_ARG, CUDA. */
+int lbm_adjoint_forward(lbm_adjoint *a, const double *phi0, int on_device, int nsteps);
+
+/* Given dL_dphi [N] (FP64, gradient of the loss with respect to the final
+ * order parameter; host or device per on_device), compute dL/dphi0 into
+ * dL_dphi0 [N] (same residence) and grads[4] (host) = {dL/dsigma, dL/dM,
+ * dL/dkappa, dL/dbeta} (sigma acts through kappa and beta, M through tau_f
+ * at fixed alpha).  The context is left at the final state.  Synchronises.
+ * Errors: STATE (no recorded run), INVALID_ARG, CUDA. */
+int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, double *dL_dphi0,
+                         double grads[4]);
+
+/* Release the recorder (not the context).  NULL-safe. */
+void lbm_adjoint_destroy(lbm_adjoint *a);
+
 /* Release the context and its device memory (synchronises first).
  * NULL-safe. */
 void lbm_destroy(lbm_ctx *ctx);

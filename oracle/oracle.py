@@ -78,6 +78,8 @@ def lib():
         L.wbo_field_lap.argtypes = [ctypes.c_void_p, dp, dp]
         L.wbo_field_mu.argtypes = [ctypes.c_void_p, dp, dp]
         L.wbo_kappa_beta.argtypes = [ctypes.c_double] * 4 + [dp, dp]
+        L.wbo_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp, dp, dp]
+        L.wbo_adjoint_init.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         L.wbo_psi.restype = ctypes.c_double
         L.wbo_psi.argtypes = [ctypes.c_double] * 4
         L.wbo_dpsi.restype = ctypes.c_double
@@ -261,3 +263,52 @@ class Oracle:
         out = np.zeros(self.N)
         lib().wbo_field_mu(self._h, _p(a), _p(out))
         return out.reshape(self.fshape)
+
+
+# ------------------------------------------------------------------ adjoint
+
+def adjoint_run(sim: Oracle, n: int, lf, lg, lS):
+    """From sim's current state run n steps, then propagate the final-state
+    adjoint (lf, lg, lS) back; returns (lf0, lg0, lS0, dpar) with
+    dpar = [dL/dkappa, dL/dbeta, dL/d(1/tau_f)] (sim ends at t + n)."""
+    lf = np.ascontiguousarray(lf, dtype=np.float64).reshape(-1).copy()
+    lg = np.ascontiguousarray(lg, dtype=np.float64).reshape(-1).copy()
+    lS = np.ascontiguousarray(lS, dtype=np.float64).reshape(-1).copy()
+    dpar = np.zeros(3)
+    lib().wbo_adjoint(sim._h, int(n), _p(lf), _p(lg), _p(lS), _p(dpar))
+    fs = sim.fshape
+    return (lf.reshape((sim.Q,) + fs), lg.reshape((sim.Q,) + fs), lS.reshape(fs), dpar)
+
+
+def adjoint_init(sim: Oracle, phi0, lf0, dpar):
+    """dL/dphi0 from the adjoint of the initial populations; adds the
+    kappa/beta terms of mu(phi0) to dpar (in place)."""
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(-1)
+    lf0 = np.ascontiguousarray(lf0, dtype=np.float64).reshape(-1)
+    out = np.zeros(sim.N)
+    lib().wbo_adjoint_init(sim._h, _p(phi0), _p(lf0), _p(out), _p(dpar))
+    return out.reshape(sim.fshape)
+
+
+def phi_loss_gradients(shape, params, phi0, target, n, lattice_name="D2Q9"):
+    """L = sum (phi^n - target)^2 from the initial condition phi0; returns
+    (L, dL/dphi0, dL/dsigma, dL/dM) by the discrete adjoint."""
+    fwd = Oracle(shape, lattice_name, **params)
+    fwd.init_phi(phi0)
+    fwd.step(n)
+    phiN = fwd.macros()["phi"]
+    loss = float(((phiN - target) ** 2).sum())
+    sim = Oracle(shape, lattice_name, **params)
+    sim.init_phi(phi0)
+    lf = np.broadcast_to(2.0 * (phiN - target), (sim.Q,) + sim.fshape)
+    lg = np.zeros((sim.Q,) + sim.fshape)
+    lS = np.zeros(sim.fshape)
+    lf0, _, _, dpar = adjoint_run(sim, n, lf, lg, lS)
+    dphi0 = adjoint_init(sim, phi0, lf0, dpar)
+    prm = dict(DEFAULTS)
+    prm.update(params)
+    d2 = (prm["phi_l"] - prm["phi_v"]) ** 2
+    dsigma = dpar[0] * 3.0 * prm["W"] / (2.0 * d2) + dpar[1] * 12.0 / (prm["W"] * d2 * d2)
+    # 1/tau_f = 1/(1/2 + M/(cs2 alpha)): d(1/tau_f)/dM = -1/(tau_f^2 cs2 alpha)
+    dM = dpar[2] * (-1.0 / (sim.tau_f ** 2 * (1.0 / 3.0) * sim.alpha))
+    return loss, dphi0, dsigma, dM

@@ -595,3 +595,275 @@ void wbo_field_mu(const wbo_sim *s, const double *phi, double *out)
     field_mu(s, phi, lap, out);
     free(lap);
 }
+
+/* =====================================================================
+ * Discrete adjoint (reverse mode) of the time step above, FP64.
+ *
+ * Not in the paper: the gradient of the discrete map, derived by
+ * differentiating each stage of the step in reverse order.  It is pinned by
+ * central finite differences of the forward map (tests), not by the paper.
+ * Loss L(f^N, g^N, S^N); the adjoint of a state is (lf, lg, lS) =
+ * (dL/df, dL/dg, dL/dS_prev) in the paper's convention.  Parameters: kappa,
+ * beta (from sigma) and 1/tau_f (from M); their adjoints accumulate in
+ * dpar = {dL/dkappa, dL/dbeta, dL/d(1/tau_f)}.
+ * ===================================================================== */
+
+/* d^2 psi / d phi^2 */
+static double d2psi(const wbo_par *P, double phi)
+{
+    const double a = phi - P->phil, b = phi - P->phiv, c = phi - 0.5 * (P->phil + P->phiv);
+    return 4.0 * P->beta * (b * c + a * c + a * b);
+}
+
+/* Transpose of the isotropic gradient (Eq. gradient): the stencil maps a
+ * scalar psi to D components; its transpose maps D components v to
+ * (G^T v)(y) = sum_i (w_i c_i / cs2) . v(y - c_i). */
+static void field_grad_T(const wbo_sim *s, const double *v, double *out)
+{
+    const wbo_lat *L = &s->L;
+    const int N = s->N;
+    for (int n = 0; n < N; ++n) out[n] = 0.0;
+    for (int x = 0; x < N; ++x)
+        for (int i = 1; i < L->Q; ++i) {
+            const int y = nbr(s, x, L->c[i]);  /* grad(x) reads psi(x + c_i) */
+            double acc = 0.0;
+            for (int a = 0; a < L->D; ++a) acc += L->w[i] * L->c[i][a] * v[a * N + x];
+            out[y] += acc / CS2;
+        }
+}
+
+/* Transpose of the Laplacian (Eq. Laplace): (L^T v)(y) = sum_x L(x, y) v(x). */
+static void field_lap_T(const wbo_sim *s, const double *v, double *out)
+{
+    const wbo_lat *L = &s->L;
+    const int N = s->N;
+    for (int n = 0; n < N; ++n) out[n] = 0.0;
+    for (int x = 0; x < N; ++x)
+        for (int i = 1; i < L->Q; ++i) {
+            const int y = nbr(s, x, L->c[i]);
+            out[y] += 2.0 * L->w[i] * v[x] / CS2;
+            out[x] -= 2.0 * L->w[i] * v[x] / CS2;
+        }
+}
+
+/* One reverse step.  On entry s holds the state at time n (f, g, S_prev)
+ * and (lf, lg, lS) the adjoint of the state at time n+1; on exit they hold
+ * the adjoint of the state at time n.  dpar accumulates. */
+static void adjoint_step(wbo_sim *s, double *lf, double *lg, double *lS, double *dpar)
+{
+    const wbo_lat *L = &s->L;
+    const wbo_par *P = &s->P;
+    const int N = s->N, Q = L->Q, D = L->D;
+    compute_macros(s);  /* phi, mu, lap, grad phi, grad mu, rho, u, p, S of time n */
+    const double drho = (P->rhol - P->rhov) / (P->phil - P->phiv);
+    const double dnu = (P->nul - P->nuv) / (P->phil - P->phiv);
+    const double itf = 1.0 / P->tauf;
+
+    double *lfs = (double *)calloc((size_t)Q * N, sizeof(double));
+    double *lgs = (double *)calloc((size_t)Q * N, sizeof(double));
+    double *lphi = (double *)calloc((size_t)N, sizeof(double));
+    double *lmu = (double *)calloc((size_t)N, sizeof(double));
+    double *lgphi = (double *)calloc((size_t)3 * N, sizeof(double));
+    double *lgmu = (double *)calloc((size_t)3 * N, sizeof(double));
+    double *tmp = (double *)calloc((size_t)N, sizeof(double));
+    double *lf_new = (double *)calloc((size_t)Q * N, sizeof(double));
+    double *lg_new = (double *)calloc((size_t)Q * N, sizeof(double));
+    double *lS_new = (double *)calloc((size_t)N, sizeof(double));
+
+    /* reverse streaming: f_i(x + c_i, n+1) = f_i*(x) */
+    for (int i = 0; i < Q; ++i)
+        for (int x = 0; x < N; ++x) {
+            const int y = nbr(s, x, L->c[i]);
+            lfs[i * N + x] = lf[i * N + y];
+            lgs[i * N + x] = lg[i * N + y];
+        }
+
+    double fe[WBO_QMAX], ge[WBO_QMAX];
+    for (int x = 0; x < N; ++x) {
+        const double phi = s->phi[x], mu = s->mu[x], rho = s->rho[x], p = s->p[x];
+        double u[3] = {0, 0, 0}, F[3] = {0, 0, 0}, grho[3] = {0, 0, 0}, gph[3] = {0, 0, 0},
+               gmu[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) {
+            u[a] = s->u[a * N + x];
+            gph[a] = s->gphi[a * N + x];
+            gmu[a] = s->gmu[a * N + x];
+            F[a] = -phi * gmu[a] + P->G[a];
+            grho[a] = drho * gph[a];
+        }
+        const double nu = lin_phase(P, phi, P->nul, P->nuv);
+        const double taug = 0.5 + nu / CS2, itg = 1.0 / taug;
+        double lu[3] = {0, 0, 0}, lF[3] = {0, 0, 0}, lgr[3] = {0, 0, 0}, lgp[3] = {0, 0, 0};
+        double lrho = 0.0, lp = 0.0, lSx = 0.0, litg = 0.0, lph = 0.0, lmux = 0.0;
+
+        /* CH collision: f* = (1 - 1/tau_f) f + f^eq/tau_f + w_i b_i (1.5 S - 0.5 S_prev) */
+        feq_node(L, phi, mu, P->alpha, fe);
+        double lsrc = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            const double l = lfs[i * N + x];
+            double cc = 0.0;
+            for (int a = 0; a < D; ++a) cc += (double)L->c[i][a] * L->c[i][a];
+            const double b = -1.0 + (cc - D * CS2) / (2.0 * CS2);
+            lf_new[i * N + x] += (1.0 - itf) * l;
+            dpar[2] += l * (fe[i] - s->f[i * N + x]);
+            lsrc += l * L->w[i] * b;
+            const double lfe = l * itf;  /* f^eq_0 = phi - (1-w0) alpha mu, f^eq_i = w_i alpha mu */
+            if (i == 0) {
+                lph += lfe;
+                lmux += -(1.0 - L->w[0]) * P->alpha * lfe;
+            } else {
+                lmux += L->w[i] * P->alpha * lfe;
+            }
+        }
+        lSx += 1.5 * lsrc;
+        lS_new[x] += -0.5 * lsrc;  /* S_prev of time n */
+        lSx += lS[x];               /* S_prev of time n+1 is S of time n */
+
+        /* NS collision: g* = (1 - 1/tau_g) g + g^eq/tau_g + (1 - 1/(2 tau_g)) Gam_i,
+         * Gam_i = w_i [u.grad rho + c.F/cs2 + ((c.u)(c.grad rho) - cs2 u.grad rho)/cs2] */
+        geq_node(L, p, rho, u, ge);
+        double ugr = 0.0, uu = 0.0;
+        for (int a = 0; a < D; ++a) {
+            ugr += u[a] * grho[a];
+            uu += u[a] * u[a];
+        }
+        for (int i = 0; i < Q; ++i) {
+            const double l = lgs[i * N + x];
+            const double gi = s->g[i * N + x];
+            double cF = 0, cu = 0, cg = 0;
+            for (int a = 0; a < D; ++a) {
+                cF += L->c[i][a] * F[a];
+                cu += L->c[i][a] * u[a];
+                cg += L->c[i][a] * grho[a];
+            }
+            const double gam = L->w[i] * (ugr + cF / CS2 + (cu * cg - CS2 * ugr) / CS2);
+            lg_new[i * N + x] += (1.0 - itg) * l;
+            litg += l * (ge[i] - gi) - 0.5 * l * gam;
+            const double lge = l * itg, lgam = l * (1.0 - 0.5 * itg);
+            /* g^eq_i = p/cs2 (w_i - delta_i0) + rho w_i [cu/cs2 + cu^2/(2 cs4) - uu/(2 cs2)] */
+            lp += lge * (L->w[i] - (i == 0 ? 1.0 : 0.0)) / CS2;
+            lrho += lge * L->w[i] * (cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2));
+            for (int a = 0; a < D; ++a) {
+                lu[a] += lge * rho * L->w[i] *
+                         (L->c[i][a] / CS2 + cu * L->c[i][a] / (CS2 * CS2) - u[a] / CS2);
+                /* Gam_i */
+                lF[a] += lgam * L->w[i] * L->c[i][a] / CS2;
+                lu[a] += lgam * L->w[i] * (grho[a] + (L->c[i][a] * cg - CS2 * grho[a]) / CS2);
+                lgr[a] += lgam * L->w[i] * (u[a] + (cu * L->c[i][a] - CS2 * u[a]) / CS2);
+            }
+        }
+        /* tau_g = 1/2 + nu(phi)/cs2 */
+        lph += litg * (-(dnu / CS2) * itg * itg);
+
+        /* S = u.grad phi */
+        for (int a = 0; a < D; ++a) {
+            lu[a] += lSx * gph[a];
+            lgp[a] += lSx * u[a];
+        }
+        /* p = cs2/(1 - w0) [sum_{i!=0} g_i + u.grad rho / 2 + rho s_0(u)],
+         * rho s_0 = -rho w0 uu / (2 cs2) */
+        {
+            const double k = CS2 / (1.0 - L->w[0]);
+            for (int i = 1; i < Q; ++i) lg_new[i * N + x] += k * lp;
+            for (int a = 0; a < D; ++a) {
+                lu[a] += k * lp * (0.5 * grho[a] - rho * L->w[0] * u[a] / CS2);
+                lgr[a] += k * lp * 0.5 * u[a];
+            }
+            lrho += k * lp * (-L->w[0] * uu / (2 * CS2));
+        }
+        /* grad rho = drho grad phi */
+        for (int a = 0; a < D; ++a) lgp[a] += drho * lgr[a];
+        /* u = (sum c g + F/2) / rho */
+        for (int a = 0; a < D; ++a) {
+            const double lj = lu[a] / rho;
+            for (int i = 0; i < Q; ++i) lg_new[i * N + x] += L->c[i][a] * lj;
+            lF[a] += 0.5 * lj;
+            lrho += -lu[a] * u[a] / rho;
+        }
+        /* F = -phi grad mu + G */
+        for (int a = 0; a < D; ++a) {
+            lph += -lF[a] * gmu[a];
+            lgmu[a * N + x] += -phi * lF[a];
+            lgphi[a * N + x] += lgp[a];
+        }
+        /* rho linear in phi */
+        lph += drho * lrho;
+        lphi[x] += lph;
+        lmu[x] += lmux;
+    }
+    /* grad mu -> mu */
+    field_grad_T(s, lgmu, tmp);
+    for (int x = 0; x < N; ++x) lmu[x] += tmp[x];
+    /* mu = dpsi(phi) - kappa lap(phi): parameters and phi */
+    for (int x = 0; x < N; ++x) {
+        dpar[0] += lmu[x] * (-s->lap[x]);
+        dpar[1] += lmu[x] * wbo_dpsi(P->beta, P->phil, P->phiv, s->phi[x]) / P->beta;
+        lphi[x] += d2psi(P, s->phi[x]) * lmu[x];
+    }
+    field_lap_T(s, lmu, tmp);
+    for (int x = 0; x < N; ++x) lphi[x] += -P->kappa * tmp[x];
+    field_grad_T(s, lgphi, tmp);
+    for (int x = 0; x < N; ++x) lphi[x] += tmp[x];
+    /* phi = sum_i f_i */
+    for (int i = 0; i < Q; ++i)
+        for (int x = 0; x < N; ++x) lf_new[i * N + x] += lphi[x];
+
+    memcpy(lf, lf_new, (size_t)Q * N * sizeof(double));
+    memcpy(lg, lg_new, (size_t)Q * N * sizeof(double));
+    memcpy(lS, lS_new, (size_t)N * sizeof(double));
+    double *bufs[] = {lfs, lgs, lphi, lmu, lgphi, lgmu, tmp, lf_new, lg_new, lS_new};
+    for (size_t k = 0; k < sizeof bufs / sizeof bufs[0]; ++k) free(bufs[k]);
+}
+
+/* From the current state (time t0), run n steps forward keeping every state,
+ * then propagate the adjoint (lf, lg, lS) of the final state back to time
+ * t0, accumulating dpar.  The simulation is left at time t0 + n. */
+void wbo_adjoint(wbo_sim *s, int n, double *lf, double *lg, double *lS, double *dpar)
+{
+    const size_t QN = (size_t)s->L.Q * s->N, N = (size_t)s->N;
+    const size_t per = 2 * QN + N;
+    double *hist = (double *)malloc((size_t)(n > 0 ? n : 1) * per * sizeof(double));
+    for (int k = 0; k < n; ++k) {
+        wbo_get_state(s, hist + k * per, hist + k * per + QN, hist + k * per + 2 * QN);
+        wbo_step(s, 1);
+    }
+    double *fin = (double *)malloc(per * sizeof(double));
+    wbo_get_state(s, fin, fin + QN, fin + 2 * QN);
+    const long t_end = s->t;
+    for (int k = n - 1; k >= 0; --k) {
+        wbo_set_state(s, hist + k * per, hist + k * per + QN, hist + k * per + 2 * QN, t_end - n + k);
+        adjoint_step(s, lf, lg, lS, dpar);
+    }
+    wbo_set_state(s, fin, fin + QN, fin + 2 * QN, t_end);
+    free(fin);
+    free(hist);
+}
+
+/* Adjoint of the initial condition (reading R9): f = f^eq(phi0, mu(phi0)),
+ * g = 0, S_prev = 0.  Given lf at time 0, returns dL/dphi0 and adds the
+ * kappa and beta contributions of mu(phi0) to dpar. */
+void wbo_adjoint_init(wbo_sim *s, const double *phi0, const double *lf, double *lphi0, double *dpar)
+{
+    const wbo_lat *L = &s->L;
+    const wbo_par *P = &s->P;
+    const int N = s->N, Q = L->Q;
+    double *mu = (double *)calloc((size_t)N, sizeof(double));
+    double *lap = (double *)calloc((size_t)N, sizeof(double));
+    double *lmu = (double *)calloc((size_t)N, sizeof(double));
+    double *tmp = (double *)calloc((size_t)N, sizeof(double));
+    field_mu(s, phi0, lap, mu);
+    for (int x = 0; x < N; ++x) {
+        lphi0[x] = lf[x];  /* f^eq_0 = phi - (1 - w0) alpha mu */
+        double l = -(1.0 - L->w[0]) * P->alpha * lf[x];
+        for (int i = 1; i < Q; ++i) l += L->w[i] * P->alpha * lf[i * N + x];
+        lmu[x] = l;
+        dpar[0] += l * (-lap[x]);
+        dpar[1] += l * wbo_dpsi(P->beta, P->phil, P->phiv, phi0[x]) / P->beta;
+        lphi0[x] += d2psi(P, phi0[x]) * l;
+    }
+    field_lap_T(s, lmu, tmp);
+    for (int x = 0; x < N; ++x) lphi0[x] += -P->kappa * tmp[x];
+    free(mu);
+    free(lap);
+    free(lmu);
+    free(tmp);
+}

@@ -29,7 +29,10 @@ LBM_FP64, LBM_FP32 = 0, 1
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_init_phi", "lbm_step", "lbm_moments",
            "lbm_diagnostics", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
            "lbm_save", "lbm_load", "lbm_sync", "lbm_time", "lbm_derived", "lbm_debug_poke",
-           "lbm_destroy", "lbm_strerror", "lbm_diagnostics_noalloc")
+           "lbm_destroy", "lbm_strerror", "lbm_diagnostics_noalloc", "lbm_batch_create",
+           "lbm_batch_case", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_shape",
+           "lbm_batch_destroy", "lbm_batch_set_shape", "lbm_adjoint_create", "lbm_adjoint_forward",
+           "lbm_adjoint_backward", "lbm_adjoint_destroy")
 
 
 class lbm_grid(ctypes.Structure):
@@ -98,6 +101,21 @@ def lib(path: str | None = None):
     L.lbm_destroy.restype = None
     L.lbm_diagnostics_noalloc.argtypes = [ctypes.POINTER(lbm_grid), ctypes.c_int,
                                           ctypes.POINTER(lbm_params), vp, vp, vp, vp, vp]
+    L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(lbm_grid),
+                                   ctypes.POINTER(lbm_params), vp, ctypes.POINTER(vp)]
+    L.lbm_batch_case.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+    L.lbm_batch_step.argtypes = [vp, ctypes.c_int]
+    L.lbm_batch_tune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_set_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_adjoint_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    L.lbm_adjoint_forward.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+    L.lbm_adjoint_backward.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
+    L.lbm_adjoint_destroy.argtypes = [vp]
+    L.lbm_adjoint_destroy.restype = None
     L.lbm_strerror.argtypes = [ctypes.c_int]
     L.lbm_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -226,3 +244,64 @@ def lbm_diagnostics_noalloc(grid, lattice, params, f, g, S_prev, out, cuda_strea
     return lib().lbm_diagnostics_noalloc(ctypes.byref(grid), int(lattice), ctypes.byref(params),
                                          addr(f), addr(g), addr(S_prev), addr(out),
                                          vp(cuda_stream or None))
+
+
+def lbm_batch_create(grids, params, cuda_stream=0):
+    """grids: list of (nx, ny); params: list of lbm_params.  Returns (rc, handle)."""
+    n = len(grids)
+    ga = (lbm_grid * n)(*[lbm_grid(g[0], g[1], 1) for g in grids])
+    pa = (lbm_params * n)(*params)
+    h = vp()
+    rc = lib().lbm_batch_create(n, ga, pa, vp(cuda_stream or None), ctypes.byref(h))
+    return rc, h
+
+
+def lbm_batch_case(b, c):
+    h = vp()
+    rc = lib().lbm_batch_case(b, int(c), ctypes.byref(h))
+    return rc, h
+
+
+def lbm_batch_step(b, n):
+    return lib().lbm_batch_step(b, int(n))
+
+
+def lbm_batch_tune(b):
+    w, r = ctypes.c_int(), ctypes.c_int()
+    rc = lib().lbm_batch_tune(b, ctypes.byref(w), ctypes.byref(r))
+    return rc, w.value, r.value
+
+
+def lbm_batch_shape(b):
+    w, r, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().lbm_batch_shape(b, ctypes.byref(w), ctypes.byref(r), ctypes.byref(t)))
+    return w.value, r.value, t.value
+
+
+def lbm_batch_set_shape(b, width, rows):
+    return lib().lbm_batch_set_shape(b, int(width), int(rows))
+
+
+def lbm_batch_destroy(b):
+    lib().lbm_batch_destroy(b)
+
+
+def lbm_adjoint_create(ctx, checkpoint_every, max_steps):
+    h = vp()
+    rc = lib().lbm_adjoint_create(ctx, int(checkpoint_every), int(max_steps), ctypes.byref(h))
+    return rc, h
+
+
+def lbm_adjoint_forward(a, phi0, on_device, nsteps):
+    return lib().lbm_adjoint_forward(a, addr(phi0), int(on_device), int(nsteps))
+
+
+def lbm_adjoint_backward(a, dL_dphi, on_device, dL_dphi0):
+    """Returns (rc, (dL/dsigma, dL/dM, dL/dkappa, dL/dbeta))."""
+    g = (ctypes.c_double * 4)()
+    rc = lib().lbm_adjoint_backward(a, addr(dL_dphi), int(on_device), addr(dL_dphi0), g)
+    return rc, tuple(g)
+
+
+def lbm_adjoint_destroy(a):
+    lib().lbm_adjoint_destroy(a)

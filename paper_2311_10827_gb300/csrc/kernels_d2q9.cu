@@ -94,6 +94,40 @@ __device__ __forceinline__ void pull9(const T *__restrict__ s, unsigned N, unsig
     v[8] = __ldg(s + (8u * N + rp + xm));  // c = (1,-1)
 }
 
+// Per-thread asynchronous copy global -> shared (4 or 8 bytes) and its
+// group fences: a thread's own copies are visible to it after wait_group.
+template <typename T>
+__device__ __forceinline__ void cp_async(T *dst, const T *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_one()
+{
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// the nine pull addresses of (x, y) (same order as pull9)
+template <typename T>
+__device__ __forceinline__ void stage9(T *dst, int stride, const T *__restrict__ s, unsigned N,
+                                       unsigned rm, unsigned r0, unsigned rp, unsigned xm,
+                                       unsigned x, unsigned xp)
+{
+    cp_async(dst + 0 * stride, s + (r0 + x));
+    cp_async(dst + 1 * stride, s + (1u * N + rp + x));
+    cp_async(dst + 2 * stride, s + (2u * N + r0 + xm));
+    cp_async(dst + 3 * stride, s + (3u * N + rm + x));
+    cp_async(dst + 4 * stride, s + (4u * N + r0 + xp));
+    cp_async(dst + 5 * stride, s + (5u * N + rm + xm));
+    cp_async(dst + 6 * stride, s + (6u * N + rm + xp));
+    cp_async(dst + 7 * stride, s + (7u * N + rp + xp));
+    cp_async(dst + 8 * stride, s + (8u * N + rp + xm));
+}
+
 // sum of the eight moving populations, fixed pairing (the rest population is
 // added last so that phi = f_0 + s keeps the small terms exact in FP32)
 template <typename T>
@@ -124,11 +158,12 @@ __device__ __forceinline__ void warp_reduce(double &sum0, double &sum1, double &
 
 // resident CTAs per SM targeted by the register budget of each precision
 // resident CTAs per SM targeted by the register budget: the FP32 time step
-// fits 64 registers (4 x 256 threads); variants carrying the FP64
-// diagnostics accumulators get more
-template <typename T, int PASS>
+// fits 64 registers (1024 threads per SM); variants carrying the FP64
+// diagnostics accumulators get 80 (768 threads), FP64 512 threads
+template <typename T, int PASS, int TX>
 struct Occ {
-    static constexpr int ctas = sizeof(T) == 4 ? ((PASS & PASS_DIAG) ? 3 : 4) : 2;
+    static constexpr int threads = sizeof(T) == 4 ? ((PASS & PASS_DIAG) ? 768 : 1024) : 512;
+    static constexpr int ctas = threads / (TX * TYB) > 0 ? threads / (TX * TYB) : 1;
 };
 
 // One tile: columns [x0, x0 + TX), rows [y0, yend), marching in direction
@@ -144,6 +179,13 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     constexpr int WM = TX + 2;      // mu ring width (halo 1)
     __shared__ T phs[R * WP];
     __shared__ T mus[R * WM];
+    // FP32: the f pulls of the next iteration's phi row are staged here by
+    // per-thread asynchronous copies (two stages) while this iteration runs
+    constexpr bool STAGE = sizeof(T) == 4;
+    constexpr int NT = TX * TYB, NFS = REST_PAIR ? 10 : 9;
+    __shared__ T fst[STAGE ? 2 * NFS * NT : 1];
+    __shared__ T fsh[STAGE ? 2 * NFS * 4 * TYB : 1];
+    const int lin = threadIdx.y * TX + threadIdx.x;
 
     const int nx = P.nx, ny = P.ny;
     const unsigned N = (unsigned)P.N;
@@ -170,11 +212,11 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
 
     // phi at row `row` for the own column (keeping the pulled values) and the
     // halo columns.
-    auto phi_row = [&](int row, T v[9], T &lo) {
+    auto phi_row = [&](int row, int sl, T v[9], T &lo) {
         const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
         const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
         const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
-        T *ph = phs + slot(row) * WP;
+        T *ph = phs + sl * WP;
         pull9(fsrc, N, rm, r0, rp, xOm, xO, xOp, v);
         lo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xO)) : T(0);
         ph[tx + 2] = v[0] + (lo + sum_moving(v));
@@ -183,6 +225,38 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
             pull9(fsrc, N, rm, r0, rp, xHm, xH, xHp, h);
             const T hlo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xH)) : T(0);
             ph[jH] = h[0] + (hlo + sum_moving(h));
+        }
+    };
+
+    // issue the copies of phi row `row`'s pulls into stage st (FP32 only)
+    auto issue_phi_row = [&](int row, int st) {
+        const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
+        const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
+        const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
+        T *d = fst + (size_t)st * NFS * NT + lin;
+        stage9(d, NT, fsrc, N, rm, r0, rp, xOm, xO, xOp);
+        if (REST_PAIR) cp_async(d + 9 * NT, fsrc + (9u * N + r0 + xO));
+        if (tx < 4) {
+            T *h = fsh + (size_t)st * NFS * 4 * TYB + ty * 4 + tx;
+            stage9(h, 4 * TYB, fsrc, N, rm, r0, rp, xHm, xH, xHp);
+            if (REST_PAIR) cp_async(h + 9 * 4 * TYB, fsrc + (9u * N + r0 + xH));
+        }
+    };
+    // phi row from stage st (the copies have landed)
+    auto phi_row_staged = [&](int sl, int st, T v[9], T &lo) {
+        T *ph = phs + sl * WP;
+        const T *d = fst + (size_t)st * NFS * NT + lin;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = d[i * NT];
+        lo = REST_PAIR ? d[9 * NT] : T(0);
+        ph[tx + 2] = v[0] + (lo + sum_moving(v));
+        if (tx < 4) {
+            const T *h = fsh + (size_t)st * NFS * 4 * TYB + ty * 4 + tx;
+            T hv[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) hv[i] = h[i * 4 * TYB];
+            const T hlo = REST_PAIR ? h[9 * 4 * TYB] : T(0);
+            ph[jH] = hv[0] + (hlo + sum_moving(hv));
         }
     };
 
@@ -198,11 +272,12 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
         const T bulk = T(4) * P.beta * (c - P.phil) * (c - P.phiv) * (c - P.phibar);
         return bulk - P.kappa * lap;
     };
-    auto mu_row = [&](int row) {
-        const T *pm = phs + slot(row - 1) * WP;
-        const T *p0 = phs + slot(row) * WP;
-        const T *pp = phs + slot(row + 1) * WP;
-        T *mr = mus + slot(row) * WM;
+    // mu at the row with ring slot s0; sm / sp are the slots of rows y-1 / y+1
+    auto mu_row = [&](int sm, int s0, int sp) {
+        const T *pm = phs + sm * WP;
+        const T *p0 = phs + s0 * WP;
+        const T *pp = phs + sp * WP;
+        T *mr = mus + s0 * WM;
         mr[tx + 1] = mu_at(pm, p0, pp, tx + 1);
         if (tx < 2) mr[jM] = mu_at(pm, p0, pp, jM);
     };
@@ -213,13 +288,27 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     // prologue: phi rows y0-2 .. y0+1 (the own row y0+ty keeps its values),
     // mu rows y0-1 .. y0
     T fcur[9], fnext[9], locur, lonext;
-    phi_row(first + dir * (ty - 2), fnext, lonext);
-    phi_row(first + dir * ty, fcur, locur);
+    phi_row(first + dir * (ty - 2), slot(first + dir * (ty - 2)), fnext, lonext);
+    phi_row(first + dir * ty, slot(first + dir * ty), fcur, locur);
     __syncthreads();
-    mu_row(first + dir * (ty - 1));
+    {
+        const int r = first + dir * (ty - 1);
+        mu_row(slot(r - 1), slot(r), slot(r + 1));
+    }
     __syncthreads();
+    if (STAGE) {
+        issue_phi_row(first + dir * (2 + ty), 0);
+        cp_commit();
+    }
 
+    // ring slot of march coordinate t + k is (rb + k) mod R with rb = (t + 2) mod R
+    int rb = 2 % R;
     for (int t = 0; t < nout; t += TYB) {
+        auto ring = [&](int k) {
+            int v = rb + k;
+            v = v >= R ? v - R : v;
+            return v < 0 ? v + R : v;
+        };
         const int row = first + dir * (t + ty);
         const bool out_ok = col_ok && t + ty < nout;
         // issue the loads of the own node first so they overlap the stencil work
@@ -233,18 +322,29 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
             if ((PASS & (PASS_STATE | PASS_DIAG)) && out_ok)
                 Sprev = __ldcs(static_cast<const T *>(a.S) + (nrow + xo));
         }
-        phi_row(first + dir * (t + 2 + ty), fnext, lonext);
+        if (STAGE) {
+            const int st = (t / TYB) & 1;
+            if (t + TYB < nout) issue_phi_row(first + dir * (t + TYB + 2 + ty), st ^ 1);
+            cp_commit();  // possibly empty: one group per iteration
+            cp_wait_all_but_one();
+            phi_row_staged(ring(2 + ty), st, fnext, lonext);
+        } else {
+            phi_row(first + dir * (t + 2 + ty), ring(2 + ty), fnext, lonext);
+        }
         __syncthreads();
-        mu_row(first + dir * (t + 1 + ty));
+        mu_row(ring(1 + ty - dir), ring(1 + ty), ring(1 + ty + dir));
         __syncthreads();
 
+        const int sm = ring(ty - dir), s0 = ring(ty), sp = ring(ty + dir);
+        rb += TYB;
+        rb = rb >= R ? rb - R : rb;
         if (out_ok) {
-            const T *pm = phs + slot(row - 1) * WP;
-            const T *p0 = phs + slot(row) * WP;
-            const T *pp = phs + slot(row + 1) * WP;
-            const T *mm = mus + slot(row - 1) * WM;
-            const T *m0 = mus + slot(row) * WM;
-            const T *mp = mus + slot(row + 1) * WM;
+            const T *pm = phs + sm * WP;
+            const T *p0 = phs + s0 * WP;
+            const T *pp = phs + sp * WP;
+            const T *mm = mus + sm * WM;
+            const T *m0 = mus + s0 * WM;
+            const T *mp = mus + sp * WM;
             const int j = tx + 2;  // phi ring index of the own column
             const int k = tx + 1;  // mu ring index of the own column
 
@@ -416,7 +516,7 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
 // Single grid: CTA (bx, by) owns strip bx and row tile by; even row tiles
 // march down, odd ones up, so neighbouring tiles meet at their shared rows.
 template <typename T, int TX, int PASS>
-__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS>::ctas))
+__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS, TX>::ctas))
     d2q9_pass_kernel(const StepParams<T> P, PassArgs a, int rows)
 {
     const int y0 = blockIdx.y * rows;
@@ -428,7 +528,7 @@ __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS>::ctas))
 // (each with its own size and parameters); buffers are picked by the step
 // parity shared by all cases.  S is read from S and written to S_out.
 template <typename T, int TX, int PASS>
-__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS>::ctas))
+__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS, TX>::ctas))
     d2q9_batch_kernel(const BatchCase *__restrict__ cases, const BatchTile *__restrict__ tiles,
                       int parity, DiagPartial *partials)
 {

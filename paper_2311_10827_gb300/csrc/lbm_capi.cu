@@ -480,8 +480,13 @@ int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out)
     if (!ctx || !out) return LBM_ERR_INVALID_ARG;
     if (!ctx->has_last_diag) return LBM_ERR_STATE;
     if (int rc = set_device(ctx)) return rc;
-    poll_diag(ctx, true);
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    // a fresh device-to-host read of the record, ordered after all queued work
+    CK(cudaMemcpyAsync(ctx->hres + 1, ctx->dres + 1, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->diag_pending = 0;
+    if (ctx->hres[1].nonfinite != 0.0 && ctx->err == LBM_OK) ctx->err = LBM_ERR_NONFINITE;
     fill_diag(ctx->hres[1], ctx->last_diag_step, out);
     return LBM_OK;
 }
@@ -712,6 +717,527 @@ const char *lbm_strerror(int code)
     case LBM_ERR_STATE: return "context not initialised";
     default: return "unknown error";
     }
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct lbm_batch {
+    int n;
+    lbm_ctx **ctx;
+    int precision;
+    int device, nsm;
+    cudaStream_t stream, cap;
+    BatchCase *d_cases;       // S_out = S (real steps)
+    BatchCase *d_cases_tune;  // S_out = scratch (tuning leaves the state unchanged)
+    BatchTile *d_tiles;
+    int tiles_cap, ntiles;
+    int width, rows, tuned;
+    cudaGraphExec_t gexec;
+    int gexec_valid;
+    int err;
+};
+
+namespace {
+
+constexpr int BATCH_GRAPH_STEPS = 32;
+
+void batch_free(lbm_batch *b)
+{
+    if (b->gexec_valid) cudaGraphExecDestroy(b->gexec);
+    if (b->d_cases) cudaFree(b->d_cases);
+    if (b->d_cases_tune) cudaFree(b->d_cases_tune);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ctx) {
+        for (int c = 0; c < b->n; ++c) lbm_destroy(b->ctx[c]);
+        free(b->ctx);
+    }
+    free(b);
+}
+
+#define BK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) {                        \
+            b->err = LBM_ERR_CUDA;                      \
+            return LBM_ERR_CUDA;                        \
+        }                                               \
+    } while (0)
+
+// tiles of every grid: strips of `width` columns, row tiles of `rows` rows,
+// row-major per grid; odd row tiles march up
+int batch_build_tiles(lbm_batch *b, int width, int rows)
+{
+    long long count = 0;
+    for (int c = 0; c < b->n; ++c) {
+        const lbm_grid &g = b->ctx[c]->grid;
+        count += (long long)((g.nx + width - 1) / width) * ((g.ny + rows - 1) / rows);
+    }
+    if (count > (1LL << 30)) return LBM_ERR_INVALID_ARG;
+    BatchTile *h = (BatchTile *)malloc((size_t)count * sizeof(BatchTile));
+    if (!h) return LBM_ERR_OOM;
+    long long k = 0;
+    for (int c = 0; c < b->n; ++c) {
+        const lbm_grid &g = b->ctx[c]->grid;
+        const int ty = (g.ny + rows - 1) / rows;
+        for (int r = 0; r < ty; ++r)
+            for (int x0 = 0; x0 < g.nx; x0 += width) {
+                BatchTile t;
+                t.c = c;
+                t.x0 = x0;
+                t.y0 = r * rows;
+                t.yend = t.y0 + rows < g.ny ? t.y0 + rows : g.ny;
+                t.dir = (r & 1) ? -1 : 1;
+                h[k++] = t;
+            }
+    }
+    if (count > b->tiles_cap) {
+        if (b->d_tiles) cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        if (cudaMalloc((void **)&b->d_tiles, (size_t)count * sizeof(BatchTile)) != cudaSuccess) {
+            free(h);
+            b->tiles_cap = 0;
+            b->err = LBM_ERR_CUDA;
+            return LBM_ERR_OOM;
+        }
+        b->tiles_cap = (int)count;
+    }
+    cudaError_t e = cudaMemcpy(b->d_tiles, h, (size_t)count * sizeof(BatchTile), cudaMemcpyHostToDevice);
+    free(h);
+    if (e != cudaSuccess) {
+        b->err = LBM_ERR_CUDA;
+        return LBM_ERR_CUDA;
+    }
+    b->ntiles = (int)count;
+    b->width = width;
+    b->rows = rows;
+    if (b->gexec_valid) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec_valid = 0;
+    }
+    return LBM_OK;
+}
+
+int batch_ready(lbm_batch *b)
+{
+    for (int c = 0; c < b->n; ++c) {
+        const lbm_ctx *x = b->ctx[c];
+        if (!x->initialized || x->cur != b->ctx[0]->cur || x->step != b->ctx[0]->step)
+            return LBM_ERR_STATE;
+        if (x->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+int batch_launch(lbm_batch *b, const BatchCase *cases, int parity, cudaStream_t st)
+{
+    BK(d2q9_batch_step(b->precision, b->width, cases, b->d_tiles, b->ntiles, parity, st));
+    return LBM_OK;
+}
+
+int batch_tune(lbm_batch *b)
+{
+    const int parity = b->ctx[0]->cur;
+    const int widths[2] = {128, 64};
+    constexpr int NR = 15;
+    const int rowsc[NR] = {8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 64, 80, 96, 128};
+    cudaEvent_t e0, e1;
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    float best = 3.4e38f;
+    int bw = 128, br = 16;
+    int rc = LBM_OK;
+    for (int wi = 0; wi < 2 && rc == LBM_OK; ++wi) {
+        for (int ri = 0; ri < NR && rc == LBM_OK; ++ri) {
+            rc = batch_build_tiles(b, widths[wi], rowsc[ri]);
+            if (rc) break;
+            for (int k = 0; k < 2 && rc == LBM_OK; ++k)
+                rc = batch_launch(b, b->d_cases_tune, parity, b->stream);
+            if (rc) break;
+            cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < 5 && rc == LBM_OK; ++k)
+                rc = batch_launch(b, b->d_cases_tune, parity, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = LBM_ERR_CUDA;
+            float ms = 0.0f;
+            if (rc == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+                best = ms;
+                bw = widths[wi];
+                br = rowsc[ri];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = batch_build_tiles(b, bw, br);
+    if (rc == LBM_OK) b->tuned = 1;
+    return rc;
+}
+
+int batch_graph(lbm_batch *b)
+{
+    if (b->gexec_valid) return LBM_OK;
+    cudaGraph_t graph = nullptr;
+    BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = LBM_OK;
+    for (int k = 0; k < BATCH_GRAPH_STEPS && rc == LBM_OK; ++k)
+        rc = batch_launch(b, b->d_cases, k & 1, b->cap);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc != LBM_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        b->err = LBM_ERR_CUDA;
+        return rc ? rc : LBM_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    BK(e);
+    b->gexec_valid = 1;
+    return LBM_OK;
+}
+
+void batch_advance(lbm_batch *b, int steps)
+{
+    for (int c = 0; c < b->n; ++c) {
+        b->ctx[c]->cur ^= (steps & 1);
+        b->ctx[c]->step += steps;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int ncases, const lbm_grid *grids, const lbm_params *params,
+                     void *cuda_stream, lbm_batch **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (ncases < 1 || !grids || !params) return LBM_ERR_INVALID_ARG;
+    for (int c = 0; c < ncases; ++c) {
+        if (int rc = validate(&grids[c], LBM_D2Q9, &params[c])) return rc;
+        if (params[c].precision != params[0].precision) return LBM_ERR_INVALID_ARG;
+    }
+    lbm_batch *b = (lbm_batch *)calloc(1, sizeof(lbm_batch));
+    if (!b) return LBM_ERR_OOM;
+    b->n = ncases;
+    b->precision = params[0].precision;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->ctx = (lbm_ctx **)calloc((size_t)ncases, sizeof(lbm_ctx *));
+    if (!b->ctx) {
+        free(b);
+        return LBM_ERR_OOM;
+    }
+    for (int c = 0; c < ncases; ++c) {
+        int rc = lbm_create(&grids[c], LBM_D2Q9, &params[c], cuda_stream, &b->ctx[c]);
+        if (rc) {
+            batch_free(b);
+            return rc;
+        }
+    }
+    b->device = b->ctx[0]->device;
+    BatchCase *h = (BatchCase *)calloc((size_t)ncases, sizeof(BatchCase));
+    if (!h) {
+        batch_free(b);
+        return LBM_ERR_OOM;
+    }
+    for (int c = 0; c < ncases; ++c) {
+        lbm_ctx *x = b->ctx[c];
+        h[c].pd = x->pd;
+        h[c].pf = x->pf;
+        h[c].f[0] = x->f[0];
+        h[c].f[1] = x->f[1];
+        h[c].g[0] = x->g[0];
+        h[c].g[1] = x->g[1];
+        h[c].S = x->S;
+        h[c].S_out = x->S;
+    }
+    const size_t bytes = (size_t)ncases * sizeof(BatchCase);
+    bool ok = cudaMalloc((void **)&b->d_cases, bytes) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_cases_tune, bytes) == cudaSuccess &&
+              cudaMemcpy(b->d_cases, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int c = 0; c < ncases && ok; ++c) h[c].S_out = b->ctx[c]->aux;  // scratch for tuning
+    ok = ok && cudaMemcpy(b->d_cases_tune, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess;
+    free(h);
+    if (!ok) {
+        cudaGetLastError();
+        batch_free(b);
+        return LBM_ERR_OOM;
+    }
+    // untuned default: 128-column strips, about one wave of 4 CTAs per SM
+    long long strip_rows = 0;
+    for (int c = 0; c < ncases; ++c)
+        strip_rows += (long long)((grids[c].nx + 127) / 128) * grids[c].ny;
+    long long rows = (strip_rows + 4LL * b->nsm - 1) / (4LL * b->nsm);
+    rows = rows < 8 ? 8 : (rows > 128 ? 128 : rows);
+    if (int rc = batch_build_tiles(b, 128, (int)(rows + (rows & 1)))) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_case(lbm_batch *b, int c, lbm_ctx **ctx)
+{
+    if (!b || !ctx || c < 0 || c >= b->n) return LBM_ERR_INVALID_ARG;
+    *ctx = b->ctx[c];
+    return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch *b, int *width, int *rows)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (int rc = batch_ready(b)) return rc;
+    if (int rc = batch_tune(b)) return rc;
+    if (width) *width = b->width;
+    if (rows) *rows = b->rows;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int n)
+{
+    if (!b || n < 0) return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (b->err) return b->err;
+    if (int rc = batch_ready(b)) return rc;
+    if (!b->tuned && n > 0)
+        if (int rc = batch_tune(b)) return rc;
+    int left = n;
+    if (left >= BATCH_GRAPH_STEPS) {
+        if (b->ctx[0]->cur == 1) {
+            if (int rc = batch_launch(b, b->d_cases, 1, b->stream)) return rc;
+            batch_advance(b, 1);
+            --left;
+        }
+        if (left >= BATCH_GRAPH_STEPS) {
+            if (int rc = batch_graph(b)) return rc;
+            const int reps = left / BATCH_GRAPH_STEPS;
+            for (int r = 0; r < reps; ++r) BK(cudaGraphLaunch(b->gexec, b->stream));
+            batch_advance(b, reps * BATCH_GRAPH_STEPS);
+            left -= reps * BATCH_GRAPH_STEPS;
+        }
+    }
+    for (; left > 0; --left) {
+        if (int rc = batch_launch(b, b->d_cases, b->ctx[0]->cur, b->stream)) return rc;
+        batch_advance(b, 1);
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_shape(const lbm_batch *b, int *width, int *rows, int *ntiles)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (width) *width = b->width;
+    if (rows) *rows = b->rows;
+    if (ntiles) *ntiles = b->ntiles;
+    return LBM_OK;
+}
+
+int lbm_batch_set_shape(lbm_batch *b, int width, int rows)
+{
+    if (!b || (width != 64 && width != 128) || rows < 2) return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (int rc = batch_build_tiles(b, width, rows)) return rc;
+    b->tuned = 1;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ adjoint
+
+struct lbm_adjoint {
+    lbm_ctx *ctx;
+    int K, max_steps, nsteps, recorded;
+    size_t snap;        // bytes of one state snapshot (f, g, S at the context's precision)
+    char *ckpt;         // (max_steps / K + 1) snapshots
+    char *seg;          // K snapshots of the segment being reversed
+    double *phi0;       // N
+    double *lf[2], *lg[2], *lS[2];
+    double *macro;      // phi, mu, p (N each), u (2N)
+    double *work;       // 7N
+    double *dpar;       // 3
+};
+
+namespace {
+
+int snapshot(lbm_ctx *ctx, char *dst, size_t snap)
+{
+    const size_t N = (size_t)ctx->N, fb = (size_t)ctx->nf * N * ctx->esz,
+                 gb = (size_t)ctx->Q * N * ctx->esz;
+    (void)snap;
+    CK(cudaMemcpyAsync(dst, ctx->f[ctx->cur], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dst + fb, ctx->g[ctx->cur], gb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dst + fb + gb, ctx->S, N * ctx->esz, cudaMemcpyDeviceToDevice, ctx->stream));
+    return LBM_OK;
+}
+
+int restore(lbm_ctx *ctx, const char *src, long long step)
+{
+    const size_t N = (size_t)ctx->N, fb = (size_t)ctx->nf * N * ctx->esz,
+                 gb = (size_t)ctx->Q * N * ctx->esz;
+    CK(cudaMemcpyAsync(ctx->f[0], src, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->g[0], src + fb, gb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->S, src + fb + gb, N * ctx->esz, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->cur = 0;
+    ctx->step = step;
+    ctx->initialized = 1;
+    return LBM_OK;
+}
+
+void adjoint_free(lbm_adjoint *a)
+{
+    void *p[] = {a->ckpt, a->seg, a->phi0, a->lf[0], a->lf[1], a->lg[0], a->lg[1],
+                 a->lS[0], a->lS[1], a->macro, a->work, a->dpar};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    free(a);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_adjoint **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctx || ctx->lattice != LBM_D2Q9 || checkpoint_every < 1 || max_steps < 1)
+        return LBM_ERR_INVALID_ARG;
+    if (int rc = set_device(ctx)) return rc;
+    lbm_adjoint *a = (lbm_adjoint *)calloc(1, sizeof(lbm_adjoint));
+    if (!a) return LBM_ERR_OOM;
+    a->ctx = ctx;
+    a->K = checkpoint_every;
+    a->max_steps = max_steps;
+    const size_t N = (size_t)ctx->N, Q = (size_t)ctx->Q;
+    a->snap = ((size_t)ctx->nf * N + Q * N + N) * ctx->esz;
+    a->snap = (a->snap + 255) / 256 * 256;
+    const size_t nck = (size_t)(max_steps / checkpoint_every + 1);
+    bool ok = cudaMalloc((void **)&a->ckpt, nck * a->snap) == cudaSuccess &&
+              cudaMalloc((void **)&a->seg, (size_t)checkpoint_every * a->snap) == cudaSuccess &&
+              cudaMalloc((void **)&a->phi0, N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&a->macro, 5 * N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&a->work, 7 * N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&a->dpar, 3 * sizeof(double)) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaMalloc((void **)&a->lf[b], Q * N * sizeof(double)) == cudaSuccess &&
+             cudaMalloc((void **)&a->lg[b], Q * N * sizeof(double)) == cudaSuccess &&
+             cudaMalloc((void **)&a->lS[b], N * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        adjoint_free(a);
+        return LBM_ERR_OOM;
+    }
+    *out = a;
+    return LBM_OK;
+}
+
+int lbm_adjoint_forward(lbm_adjoint *a, const double *phi0, int on_device, int nsteps)
+{
+    if (!a || !phi0 || nsteps < 0 || nsteps > a->max_steps) return LBM_ERR_INVALID_ARG;
+    lbm_ctx *ctx = a->ctx;
+    if (int rc = set_device(ctx)) return rc;
+    const size_t N = (size_t)ctx->N;
+    CK(cudaMemcpyAsync(a->phi0, phi0, N * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    if (int rc = lbm_init_phi(ctx, a->phi0, 1)) return rc;
+    for (int done = 0, k = 0; done <= nsteps; done += a->K, ++k) {
+        if (int rc = snapshot(ctx, a->ckpt + (size_t)k * a->snap, a->snap)) return rc;
+        const int m = nsteps - done < a->K ? nsteps - done : a->K;
+        if (m > 0)
+            if (int rc = lbm_step(ctx, m)) return rc;
+        if (m < a->K) break;
+    }
+    a->nsteps = nsteps;
+    a->recorded = 1;
+    return LBM_OK;
+}
+
+int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, double *dL_dphi0,
+                         double grads[4])
+{
+    if (!a || !dL_dphi || !dL_dphi0 || !grads) return LBM_ERR_INVALID_ARG;
+    if (!a->recorded) return LBM_ERR_STATE;
+    lbm_ctx *ctx = a->ctx;
+    if (int rc = set_device(ctx)) return rc;
+    const size_t N = (size_t)ctx->N;
+    const int nx = ctx->grid.nx, ny = ctx->grid.ny;
+    // the seed: dL/dphi of the final state into the adjoint of every f_i
+    double *seed = a->work;
+    CK(cudaMemcpyAsync(seed, dL_dphi, N * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    int cb = 0;
+    CK(adj_d2q9_seed((int)N, seed, a->lf[cb], a->lg[cb], a->lS[cb], ctx->stream));
+    CK(cudaMemsetAsync(a->dpar, 0, 3 * sizeof(double), ctx->stream));
+    double *phi = a->macro, *mu = a->macro + N, *p = a->macro + 2 * N, *u = a->macro + 3 * N;
+    const int nseg = (a->nsteps + a->K - 1) / a->K;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int t0 = sgi * a->K;
+        const int len = a->nsteps - t0 < a->K ? a->nsteps - t0 : a->K;
+        // recompute the segment forward, keeping every state
+        if (int rc = restore(ctx, a->ckpt + (size_t)sgi * a->snap, t0)) return rc;
+        for (int j = 0; j < len; ++j) {
+            if (int rc = snapshot(ctx, a->seg + (size_t)j * a->snap, a->snap)) return rc;
+            if (j + 1 < len)
+                if (int rc = lbm_step(ctx, 1)) return rc;
+        }
+        // reverse through it
+        for (int j = len - 1; j >= 0; --j) {
+            if (int rc = restore(ctx, a->seg + (size_t)j * a->snap, t0 + j)) return rc;
+            if (int rc = run_pass(ctx, PASS_MACROS, ctx->stream, phi, p, u, mu)) return rc;
+            CK(adj_d2q9_step(ctx->prm.precision, &ctx->pd, nx, ny, ctx->f[0], ctx->g[0], ctx->S,
+                             phi, mu, p, u, a->lf[cb], a->lg[cb], a->lS[cb], a->lf[cb ^ 1],
+                             a->lg[cb ^ 1], a->lS[cb ^ 1], a->work, a->dpar, ctx->stream));
+            cb ^= 1;
+        }
+    }
+    // initial condition f = f^eq(phi0, mu(phi0))
+    double *lphi0 = on_device ? dL_dphi0 : a->macro;
+    CK(adj_d2q9_init(&ctx->pd, nx, ny, a->phi0, a->lf[cb], a->work, lphi0, a->dpar, ctx->stream));
+    double dp[3];
+    CK(cudaMemcpyAsync(dp, a->dpar, sizeof dp, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device)
+        CK(cudaMemcpyAsync(dL_dphi0, lphi0, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    // leave the context at the final state
+    if (int rc = restore(ctx, a->ckpt + (size_t)(a->nsteps / a->K) * a->snap,
+                         (long long)(a->nsteps / a->K) * a->K))
+        return rc;
+    if (a->nsteps % a->K)
+        if (int rc = lbm_step(ctx, a->nsteps % a->K)) return rc;
+    const lbm_params &pr = ctx->prm;
+    const double d2 = (pr.phi_l - pr.phi_v) * (pr.phi_l - pr.phi_v);
+    grads[2] = dp[0];
+    grads[3] = dp[1];
+    grads[0] = dp[0] * 3.0 * pr.W / (2.0 * d2) + dp[1] * 12.0 / (pr.W * d2 * d2);
+    // 1/tau_f with tau_f = 1/2 + M/(cs2 alpha): d(1/tau_f)/dM = -1/(tau_f^2 cs2 alpha)
+    grads[1] = dp[2] * (-1.0 / (ctx->tau_f * ctx->tau_f * CS2 * ctx->alpha));
+    return LBM_OK;
+}
+
+void lbm_adjoint_destroy(lbm_adjoint *a)
+{
+    if (!a) return;
+    cudaSetDevice(a->ctx->device);
+    cudaStreamSynchronize(a->ctx->stream);
+    adjoint_free(a);
 }
 
 }  // extern "C"

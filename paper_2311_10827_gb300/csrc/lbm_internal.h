@@ -92,6 +92,20 @@ cudaError_t d3q19_get_state(int precision, const void *params, const void *f, co
 cudaError_t d3q19_set_state(int precision, const void *params, void *f, void *g, void *S,
                             const double *fi, const double *gi, const double *Si, cudaStream_t st);
 
+// D2Q9 discrete adjoint (kernels_adjoint.cu); FP64 adjoint fields in the
+// paper's convention; work holds 7 N doubles; dpar accumulates
+// {dL/dkappa, dL/dbeta, dL/d(1/tau_f)}
+cudaError_t adj_d2q9_seed(int N, const double *dphi, double *lf, double *lg, double *lS,
+                          cudaStream_t st);
+cudaError_t adj_d2q9_step(int precision, const void *params64, int nx, int ny, const void *f,
+                          const void *g, const void *S, const double *phi, const double *mu,
+                          const double *p, const double *u, const double *lf_in,
+                          const double *lg_in, const double *lS_in, double *lf_out, double *lg_out,
+                          double *lS_out, double *work, double *dpar, cudaStream_t st);
+cudaError_t adj_d2q9_init(const void *params64, int nx, int ny, const double *phi0,
+                          const double *lf, double *work, double *lphi0, double *dpar,
+                          cudaStream_t st);
+
 // diagnostics reduction (kernels_diag.cu): partials[n] -> out (one record)
 cudaError_t diag_reduce(const DiagPartial *partials, int n, DiagPartial *out, cudaStream_t st);
 

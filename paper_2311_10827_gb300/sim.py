@@ -31,14 +31,15 @@ def make_params(precision="fp32", diag_every=0, **kw) -> capi.lbm_params:
 
 
 class Simulation:
-    """One periodic grid on the current CUDA device.
+    """One periodic grid on the current CUDA device (or, with ``_borrow``, a
+    view of a grid owned by a :class:`Batch`).
 
     ``shape`` is (nx, ny) or (nx, ny, nz).  ``stream`` is a raw cudaStream_t
     (e.g. ``torch.cuda.current_stream().cuda_stream``) or 0.
     """
 
     def __init__(self, shape, lattice="D2Q9", precision="fp32", stream=0, diag_every=0,
-                 **params):
+                 _borrow=None, **params):
         self.shape = tuple(shape)
         nx, ny = shape[0], shape[1]
         nz = shape[2] if len(shape) > 2 else 1
@@ -47,8 +48,12 @@ class Simulation:
         self.Q = 9 if lattice == "D2Q9" else 19
         self.precision = precision
         self.params = make_params(precision, diag_every, **params)
-        rc, h = capi.lbm_create((nx, ny, nz), LATTICES[lattice], self.params, stream)
-        capi.check(rc, "lbm_create")
+        self._owned = _borrow is None
+        if _borrow is None:
+            rc, h = capi.lbm_create((nx, ny, nz), LATTICES[lattice], self.params, stream)
+            capi.check(rc, "lbm_create")
+        else:
+            h = _borrow
         self._h = h
         self.kappa, self.beta, self.tau_f, self.alpha = capi.lbm_derived(h)
 
@@ -70,7 +75,8 @@ class Simulation:
 
     def close(self):
         if getattr(self, "_h", None):
-            capi.lbm_destroy(self._h)
+            if getattr(self, "_owned", True):
+                capi.lbm_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -147,3 +153,61 @@ class Simulation:
 
     def load(self, buf: np.ndarray):
         capi.check(capi.lbm_load(self._h, np.ascontiguousarray(buf)), "lbm_load")
+
+
+class Batch:
+    """Many independent D2Q9 grids advanced by one launch per step.
+
+    ``cases`` is a list of ``(shape, params_dict)``; all at ``precision``.
+    ``batch.case(i)`` is a :class:`Simulation` view of grid i (initialise,
+    read moments, diagnostics, state) owned by the batch.
+    """
+
+    def __init__(self, cases, precision="fp32", stream=0):
+        self.shapes = [tuple(sh) for sh, _ in cases]
+        plist = [make_params(precision, 0, **prm) for _, prm in cases]
+        rc, h = capi.lbm_batch_create(self.shapes, plist, stream)
+        capi.check(rc, "lbm_batch_create")
+        self._h = h
+        self._cases = []
+        for i, (sh, prm) in enumerate(cases):
+            rc, ch = capi.lbm_batch_case(h, i)
+            capi.check(rc, "lbm_batch_case")
+            self._cases.append(Simulation(sh, precision=precision, _borrow=ch, **prm))
+
+    def __len__(self):
+        return len(self._cases)
+
+    def case(self, i) -> Simulation:
+        return self._cases[i]
+
+    def step(self, n=1):
+        capi.check(capi.lbm_batch_step(self._h, n), "lbm_batch_step")
+
+    def tune(self):
+        rc, w, r = capi.lbm_batch_tune(self._h)
+        capi.check(rc, "lbm_batch_tune")
+        return w, r
+
+    def shape(self):
+        return capi.lbm_batch_shape(self._h)
+
+    def set_shape(self, width, rows):
+        capi.check(capi.lbm_batch_set_shape(self._h, width, rows), "lbm_batch_set_shape")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for c in self._cases:
+                c._h = None
+            capi.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
