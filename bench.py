@@ -46,6 +46,11 @@ RATIOS = (10.0, 100.0)
 # bytes moved per node update: f, g read + write (4 Q s) and S read + write;
 # FP32 also moves the low word of the rest population pair (8 B)
 BYTES_PER_NODE = {"fp32": 160, "fp64": 304}
+# D3Q19: FP32 4 Q 4 + 8 (rest pair low word) + 8 (S); FP64 4 Q 8 + 16; 16-bit
+# offsets: 4 Q 2 + 2 x 24 (six FP32 macros read and written) + 8 (S)
+BYTES_PER_NODE_3D = {"fp32": 320, "fp64": 624, "f16off": 208, "bf16off": 208}
+DTYPE = {"fp32": "f32", "fp64": "f64", "f16off": "f32 (f16 offset storage)",
+         "bf16off": "f32 (bf16 offset storage)"}
 KERNEL_SOURCES = ("paper_2311_10827_gb300/csrc/kernels_d2q9.cu",)
 TRAFFIC_KERNEL = "d2q9_batch_kernel"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_d2q9_fp32_droplet1024.txt")
@@ -406,6 +411,177 @@ def run_ensemble(args, rank, world, local_rank):
     b.close()
 
 
+def run_coalescence3d(args, rank, world, local_rank):
+    """3D coalescence (workloads.COALESCENCE_3D): 512^3 periodic, D3Q19 for
+    both populations, two droplets R = 64, centres 2R + 3 apart, W = 5,
+    density ratio 10.  One step = the phi pass and the fused pass; `value`
+    and the roofline use the device time of whole steps (both kernels)."""
+    import torch
+
+    from paper_2311_10827_gb300 import build as B
+    B.build()
+    from paper_2311_10827_gb300 import capi
+    from paper_2311_10827_gb300 import workloads as wl
+    from paper_2311_10827_gb300.sim import Simulation
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    cfg = wl.COALESCENCE_3D
+    n = args.size or cfg["shape"][0]
+    R = cfg["R"] * n / cfg["shape"][0]
+    sim = Simulation((n, n, n), lattice="D3Q19", precision=args.precision,
+                     stream=stream.cuda_stream, **wl.physical(cfg))
+    # phi0 of Section 3.3 in 3D, built on the device in FP64
+    ax = torch.arange(n, dtype=torch.float64, device=dev)
+    off = R + 0.5 * cfg["gap"]
+    phi = torch.ones((), dtype=torch.float64, device=dev)
+    for xk in (0.5 * n - off, 0.5 * n + off):
+        d = torch.sqrt((ax[None, None, :] - xk) ** 2 + (ax[None, :, None] - 0.5 * n) ** 2
+                       + (ax[:, None, None] - 0.5 * n) ** 2) - R
+        phi = phi - torch.tanh(2 * d / cfg["W"])
+        del d
+    phi = (0.5 + 0.5 * phi).contiguous()
+    sim.init_phi(phi)
+    del phi
+    torch.cuda.empty_cache()
+    plan = []
+    left = args.steps
+    while left > 0:
+        plan.append(min(args.diag_every, left))
+        left -= plan[-1]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in plan]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d_first = None
+    with ClockSampler(local_rank) as clk:
+        sim.step(args.warmup)
+        d_first = sim.diagnostics()
+        torch.cuda.synchronize()
+        t_start = time.time()
+        t0.record(stream)
+        for (a, b), m in zip(ev, plan):
+            a.record(stream)
+            sim.step(m)
+            b.record(stream)
+            rc, d = capi.lbm_diagnostics(sim.handle)
+            capi.check(rc)
+            if d.nonfinite:
+                raise RuntimeError("non-finite fields in the timed run")
+        t1.record(stream)
+        torch.cuda.synchronize()
+        t_end = time.time()
+    d_last = d.as_dict()
+    total_s = max_over_ranks_dist(t0.elapsed_time(t1) / 1e3, world, dev)
+    step_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps
+    nodes = n ** 3
+    sim.close()
+    if rank != 0:
+        return
+    peaks, src = measured_peaks()
+    bpn = BYTES_PER_NODE_3D[args.precision]
+    achieved = bpn * nodes / step_s / 1e9
+    print(json.dumps({
+        "metric": "MLUPS (fused f+g step)", "value": nodes * args.steps * world / total_s / 1e6,
+        "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"3D coalescence of two droplets, D3Q19, {n}^3 periodic, "
+                               f"R={R:g}, centres 2R+3 apart, W=5, rho_l/rho_v=10, "
+                               "nu_l/nu_v=10, sigma=1e-3, M=0.05",
+                   "lattice": "D3Q19", "nodes_per_step": nodes, "diag_every": args.diag_every,
+                   "l2": "inputs larger than L2, steps back to back"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": f"{src} copy bandwidth (hbm_gbs)",
+                     "algorithmic_bytes_per_node": bpn, "step_ms": step_s * 1e3,
+                     "kernel": ("d3q19_off_phi_kernel + d3q19_off_pass_kernel" if "off" in args.precision
+                                else "d3q19_phi_kernel + d3q19_pass_kernel") + " (whole step)"},
+        "mass_drift_rel": (d_last["sum_phi"] - d_first["sum_phi"]) / d_first["sum_phi"],
+        "u_max_final": d_last["u_max"],
+        "clocks": clk.summary(t_start, t_end),
+        "gpu_launches": 2 * args.steps + 2 * len(plan),
+    }), flush=True)
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """Gradient of L = sum (phi_N - phi_target)^2 with respect to phi0, sigma
+    and M through the discrete adjoint (workloads.COALESCENCE_ADJ: 512^2, two
+    droplets R = 48, centres 2R + W apart; checkpoints every 100 steps).  The
+    target is the final phi of a run from phi0 + 1e-3 N(0, 1), default_rng(0).
+    `value` counts node updates of the differentiated run per second of
+    forward + backward; the plain forward of the same run is timed beside it."""
+    import numpy as np
+    import torch
+
+    from paper_2311_10827_gb300 import build as B
+    B.build()
+    from paper_2311_10827_gb300 import workloads as wl
+    from paper_2311_10827_gb300.adjoint import rollout
+    from paper_2311_10827_gb300.sim import Simulation
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg = wl.COALESCENCE_ADJ
+    nx, ny = cfg["shape"]
+    prm = wl.physical(cfg)
+    sigma0, M0 = prm.pop("sigma"), prm.pop("M")
+    phi0 = wl.two_droplets(nx, ny, cfg["R"], cfg["W"])
+    noisy = phi0 + 1e-3 * np.random.default_rng(0).standard_normal(phi0.shape)
+    nsteps = args.steps
+    ts = Simulation((nx, ny), precision=args.precision, sigma=sigma0, M=M0, **prm)
+    ts.init_phi(noisy)
+    ts.step(nsteps)
+    target = torch.tensor(ts.moments()["phi"], device=dev)
+    ts.close()
+    p0 = torch.tensor(phi0, device=dev)
+
+    def one():
+        x = p0.clone().requires_grad_(True)
+        sg = torch.tensor(sigma0, dtype=torch.float64, device=dev, requires_grad=True)
+        mo = torch.tensor(M0, dtype=torch.float64, device=dev, requires_grad=True)
+        phiN = rollout(x, sg, mo, shape=(nx, ny), nsteps=nsteps, checkpoint_every=100,
+                       precision=args.precision, **prm)
+        L = ((phiN - target) ** 2).sum()
+        L.backward()
+        return float(L.detach()), x.grad, float(sg.grad), float(mo.grad)
+
+    one()  # warm-up (builds graphs, touches allocations)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    L, g0, gs, gm = one()
+    torch.cuda.synchronize()
+    t_grad = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    fs = Simulation((nx, ny), precision=args.precision, sigma=sigma0, M=M0, **prm)
+    fs.init_phi(phi0)
+    fs.step(args.warmup)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    fs.step(nsteps)
+    fs.sync()
+    t_fwd = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    fs.close()
+    if rank != 0:
+        return
+    nodes = nx * ny
+    print(json.dumps({
+        "metric": "MLUPS (fused f+g step), differentiated: forward + adjoint",
+        "value": nodes * nsteps * world / t_grad / 1e6, "unit": "MLUPS", "n_gpus": world,
+        "steps": nsteps, "warmup": 1, "ms_per_step": t_grad / nsteps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"2D two-droplet coalescence {nx}x{ny}, R=48, W=8, "
+                               "sigma=5e-3, M=0.1, rho_l/rho_v=10, nu_l/nu_v=1; loss = "
+                               "sum (phi_N - phi_target)^2, target from phi0 + 1e-3 N(0,1) "
+                               "(default_rng(0)); checkpoint every 100 steps"},
+        "gradient_s": t_grad, "forward_only_s": t_fwd,
+        "plain_step_MLUPS": nodes * nsteps / t_fwd / 1e6,
+        "cost_vs_plain_forward": t_grad / t_fwd,
+        "loss": L, "dL_dsigma": gs, "dL_dM": gm,
+        "dL_dphi0_norm": float(g0.norm()),
+    }), flush=True)
+
+
 def max_over_ranks_dist(x, world, device):
     """Max of a float over the ranks (identity for one rank)."""
     if world <= 1:
@@ -430,13 +606,18 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "f16off", "bf16off"], default="fp32",
+                    help="f16off / bf16off: 16-bit offset storage (coalescence3d only)")
     ap.add_argument("--diag-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="WxR: fixed batch tile shape instead of the "
                     "autotuner (profiling commands use the shape the tuner picked)")
-    ap.add_argument("--workload", choices=["droplet1024", "ensemble"], default="droplet1024",
-                    help="droplet1024: the headline line; ensemble: the 256-grid batch")
+    ap.add_argument("--workload", choices=["droplet1024", "ensemble", "coalescence3d", "adjoint"],
+                    default="droplet1024",
+                    help="droplet1024: the headline line; ensemble: the 256-grid batch; "
+                         "coalescence3d: the 512^3 D3Q19 run; adjoint: the 512^2 gradient")
+    ap.add_argument("--size", type=int, default=0,
+                    help="coalescence3d: edge of the cube (default 512)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -446,6 +627,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if "off" in args.precision and args.workload != "coalescence3d":
+        ap.error("offset storage is built for the D3Q19 path (--workload coalescence3d)")
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -454,6 +637,10 @@ def main():
     try:
         if args.workload == "ensemble":
             run_ensemble(args, rank, world, local_rank)
+        elif args.workload == "coalescence3d":
+            run_coalescence3d(args, rank, world, local_rank)
+        elif args.workload == "adjoint":
+            run_adjoint(args, rank, world, local_rank)
         else:
             run_native(args, rank, world, local_rank)
     finally:

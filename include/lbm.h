@@ -67,8 +67,21 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 /* Precision of storage and arithmetic.  LBM_FP64: FP64 throughout (parity
  * form).  LBM_FP32: FP32 populations and arithmetic, the rest population of
  * f kept as a compensated pair of FP32 words (its per-step change near
- * equilibrium is below half an FP32 ulp of phi); diagnostics in FP64. */
-typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
+ * equilibrium is below half an FP32 ulp of phi); diagnostics in FP64.
+ * LBM_FP32_F16OFF / LBM_FP32_BF16OFF (D3Q19 only): FP32 arithmetic with every
+ * population stored as a 16-bit (FP16 / BF16) offset from its equilibrium
+ * (Eq. H_i for f, the g^eq of Eq. G_i for g), evaluated at FP32 macroscopic
+ * fields (phi, mu, p, u) stored with the state; each population field has a
+ * power-of-two scale, refreshed from the largest offset whenever diagnostics
+ * run.  The rest population keeps phi's rounding residual in its offset (the
+ * compensated pair of LBM_FP32).  Not a form of the paper: a storage format
+ * that cuts the bytes moved per node update. */
+typedef enum {
+    LBM_FP64 = 0,
+    LBM_FP32 = 1,
+    LBM_FP32_F16OFF = 2,
+    LBM_FP32_BF16OFF = 3
+} lbm_precision;
 
 /* The paper's statement of the problem (Section 2 and Section 3):
  *   W      interface thickness (Eq. beta)
@@ -126,7 +139,8 @@ int lbm_params_default(lbm_params *out);
  * is a cudaStream_t (NULL = legacy default stream) on which all later work is
  * issued.  Errors: INVALID_ARG (NULL pointers, non-positive sizes, nz != 1
  * for D2Q9, W <= 0, sigma < 0, M <= 0 or alpha <= 0 when tau_f is derived,
- * tau_f <= 1/2, phi_l == phi_v, rho <= 0, nu <= 0, unknown precision),
+ * tau_f <= 1/2, phi_l == phi_v, rho <= 0, nu <= 0, unknown precision, an
+ * offset precision with D2Q9),
  * OOM, CUDA (no usable GPU).  Validation happens before any CUDA call, so a
  * host without a GPU reports INVALID_ARG for a bad problem. */
 int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params,
@@ -204,8 +218,10 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g,
 
 /* Checkpoint to / restore from a host buffer in the library's own format
  * (header, then the raw device state at the context's precision: f, g, S_prev
- * in the storage layout described at lbm_diagnostics_noalloc; a restore is
- * bit-exact).  lbm_save with buf == NULL stores the required size in *bytes.
+ * in the storage layout described at lbm_diagnostics_noalloc; for the offset
+ * precisions f is the Q offset arrays (u16), the D + 3 FP32 macro arrays
+ * (phi, mu, p, u), each padded to 256 bytes, and the two FP32 scales padded
+ * to 256 bytes, and g is the Q offset arrays; a restore is bit-exact).  lbm_save with buf == NULL stores the required size in *bytes.
  * lbm_load checks that grid, lattice and precision match.  Errors:
  * INVALID_ARG (size or header mismatch), STATE, CUDA. */
 int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes);
@@ -279,7 +295,9 @@ void lbm_batch_destroy(lbm_batch *b);
  * then, given dL/dphi of the final state, returns dL/dphi0 and the gradients
  * with respect to the surface tension and the mobility.  Segments between
  * checkpoints are recomputed forward on the backward pass; the reverse step
- * runs in FP64 whatever the context's precision.
+ * runs at the context's precision (FP64 adjoint fields and arithmetic for an
+ * FP64 context, FP32 for an FP32 one); parameter gradients accumulate in
+ * FP64.
  * ------------------------------------------------------------------------- */
 typedef struct lbm_adjoint lbm_adjoint;
 

@@ -17,8 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
-SOURCES = ["lbm_capi.cu", "kernels_d2q9.cu", "kernels_d3q19.cu", "kernels_diag.cu",
-           "kernels_adjoint.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_capi.cu", "kernels_d2q9.cu", "kernels_d3q19.cu", "kernels_d3q19_off.cu",
+           "kernels_diag.cu", "kernels_adjoint.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -23,7 +23,7 @@ LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_FP64, LBM_FP32 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP32_F16OFF, LBM_FP32_BF16OFF = 0, 1, 2, 3
 
 # every symbol declared in include/lbm.h
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_init_phi", "lbm_step", "lbm_moments",

@@ -2,8 +2,10 @@
 // loss on the final order parameter with respect to the initial field phi0,
 // the surface tension (through kappa and beta) and the mobility (through
 // 1/tau_f).  Not in the paper: the derivative of the discrete map, stage by
-// stage in reverse order.  Adjoint arithmetic is FP64; the forward state is
-// read at its own precision.  Adjoint fields use the paper's convention
+// stage in reverse order.  Adjoint arithmetic and adjoint fields are in the
+// context's precision (FP64, or FP32 for the FP32 form; the parameter
+// gradients accumulate in FP64); the forward state is read at its own
+// precision.  Adjoint fields use the paper's convention
 // (pre-collision populations f_i(x, t), [Q][N]).
 //
 // One reverse step (state at time n, adjoint of the state at n + 1):
@@ -54,113 +56,128 @@ __device__ __forceinline__ unsigned at(const AdjGeom &g, int x, int y, int dx, i
 }
 
 // isotropic gradient of an FP64 field at (x, y): (1/cs2) sum w_i c_i psi(x + c_i)
-__device__ __forceinline__ void grad_at(const AdjGeom &g, const double *psi, int x, int y,
-                                        double &gx, double &gy)
+template <typename R>
+__device__ __forceinline__ void grad_at(const AdjGeom &g, const double *psi, int x, int y, R &gx,
+                                        R &gy)
 {
-    gx = 0.0, gy = 0.0;
+    gx = R(0), gy = R(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const double v = psi[at(g, x, y, cxa(i), cya(i))];
-        gx += wa(i) * cxa(i) * v;
-        gy += wa(i) * cya(i) * v;
+        const R v = (R)psi[at(g, x, y, cxa(i), cya(i))];
+        gx += R(wa(i) * cxa(i) / CS2A) * v;
+        gy += R(wa(i) * cya(i) / CS2A) * v;
     }
-    gx /= CS2A;
-    gy /= CS2A;
+}
+
+// one FP64 atomic per block for a per-thread partial (warp shuffles, then
+// the warps' sums in shared memory); every thread of the block calls it
+__device__ __forceinline__ void block_add(double v, double *dst)
+{
+    __shared__ double part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();  // part[] may still be read by an earlier call
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        if (s != 0.0) atomicAdd(dst, s);
+    }
 }
 
 // lambda_phi, lambda_mu, lambda_grad phi, lambda_grad mu and dL/d(1/tau_f)
-template <typename T>
+template <typename T, typename R>
 __global__ void adj_local(const StepParams<double> P, AdjGeom geo, const T *__restrict__ f,
-                          const T *__restrict__ g, const T *__restrict__ S, int rest_pair,
-                          const double *__restrict__ phi, const double *__restrict__ mu,
-                          const double *__restrict__ pf, const double *__restrict__ uf,
-                          const double *__restrict__ lf_in, const double *__restrict__ lg_in,
-                          const double *__restrict__ lS_in, double *__restrict__ lf_out,
-                          double *__restrict__ lg_out, double *__restrict__ lS_out,
-                          double *__restrict__ lphi, double *__restrict__ lmu,
-                          double *__restrict__ lgphi, double *__restrict__ lgmu, double *dpar)
+                          const T *__restrict__ g, int rest_pair, const double *__restrict__ phi,
+                          const double *__restrict__ mu, const double *__restrict__ pf,
+                          const double *__restrict__ uf, const R *__restrict__ lf_in,
+                          const R *__restrict__ lg_in, const R *__restrict__ lS_in,
+                          R *__restrict__ lf_out, R *__restrict__ lg_out, R *__restrict__ lS_out,
+                          R *__restrict__ lphi, R *__restrict__ lmu, R *__restrict__ lgphi,
+                          R *__restrict__ lgmu, double *dpar)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned N = geo.N;
-    double itf_part = 0.0;
+    constexpr R IC = R(1.0 / CS2A);
+    R itf_part = R(0);
     if (n < N) {
         const int x = n % geo.nx, y = n / geo.nx;
-        const double ph = phi[n], m = mu[n], p = pf[n];
-        const double u[2] = {uf[n], uf[N + n]};
-        double gph[2], gmu[2];
+        const R ph = (R)phi[n], m = (R)mu[n], p = (R)pf[n];
+        const R u[2] = {(R)uf[n], (R)uf[N + n]};
+        R gph[2], gmu[2];
         grad_at(geo, phi, x, y, gph[0], gph[1]);
         grad_at(geo, mu, x, y, gmu[0], gmu[1]);
-        const double drho = P.drho, dnu = P.dnu;
-        const double rho = P.rhov + (ph - P.phiv) * drho;
-        const double nu = P.nuv + (ph - P.phiv) * dnu;
-        const double itg = 1.0 / (0.5 + nu / CS2A);
-        const double itf = P.inv_tauf, alpha = P.alpha;
-        const double F[2] = {-ph * gmu[0] + P.G[0], -ph * gmu[1] + P.G[1]};
-        const double gr[2] = {drho * gph[0], drho * gph[1]};
-        const double ugr = u[0] * gr[0] + u[1] * gr[1], uu = u[0] * u[0] + u[1] * u[1];
+        const R drho = (R)P.drho, dnu = (R)P.dnu;
+        const R rho = (R)P.rhov + (ph - (R)P.phiv) * drho;
+        const R nu = (R)P.nuv + (ph - (R)P.phiv) * dnu;
+        const R itg = R(1) / (R(0.5) + nu * IC);
+        const R itf = (R)P.inv_tauf, alpha = (R)P.alpha;
+        const R F[2] = {-ph * gmu[0] + (R)P.G[0], -ph * gmu[1] + (R)P.G[1]};
+        const R gr[2] = {drho * gph[0], drho * gph[1]};
+        const R ugr = u[0] * gr[0] + u[1] * gr[1], uu = u[0] * u[0] + u[1] * u[1];
 
         // forward populations of time n at x (pull layout: f_i(x) stored at x - c_i)
-        double fv[9], gv[9];
+        R fv[9], gv[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const unsigned src = at(geo, x, y, -cxa(i), -cya(i));
-            fv[i] = (double)f[i * N + src];
-            gv[i] = (double)g[i * N + src];
+            fv[i] = (R)f[i * N + src];
+            gv[i] = (R)g[i * N + src];
         }
-        if (rest_pair) fv[0] += (double)f[9 * N + n];
-        const double Sprev = (double)S[n];
-        (void)Sprev;
+        if (rest_pair) fv[0] += (R)f[9 * N + n];
 
-        double lu[2] = {0, 0}, lF[2] = {0, 0}, lgr[2] = {0, 0}, lgp[2] = {0, 0};
-        double lrho = 0, lp = 0, lSx = 0, litg = 0, lph = 0, lmux = 0, lsrc = 0;
+        R lu[2] = {0, 0}, lF[2] = {0, 0}, lgr[2] = {0, 0}, lgp[2] = {0, 0};
+        R lrho = 0, lp = 0, lSx = 0, litg = 0, lph = 0, lmux = 0, lsrc = 0;
 
         // CH collision: f* = (1 - 1/tau_f) f + f^eq/tau_f + w_i b_i (1.5 S - 0.5 S_prev)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double l = lf_in[i * N + at(geo, x, y, cxa(i), cya(i))];  // reverse streaming
-            const double fe = i == 0 ? ph - (1.0 - wa(0)) * alpha * m : wa(i) * alpha * m;
-            lf_out[i * N + n] = (1.0 - itf) * l;
+            const R l = lf_in[i * N + at(geo, x, y, cxa(i), cya(i))];  // reverse streaming
+            const R fe = i == 0 ? ph - R(1.0 - wa(0)) * alpha * m : R(wa(i)) * alpha * m;
+            lf_out[i * N + n] = (R(1) - itf) * l;
             itf_part += l * (fe - fv[i]);
-            lsrc += l * wa(i) * ba(i);
-            const double lfe = l * itf;
+            lsrc += l * R(wa(i) * ba(i));
+            const R lfe = l * itf;
             if (i == 0) {
                 lph += lfe;
-                lmux += -(1.0 - wa(0)) * alpha * lfe;
+                lmux += -R(1.0 - wa(0)) * alpha * lfe;
             } else {
-                lmux += wa(i) * alpha * lfe;
+                lmux += R(wa(i)) * alpha * lfe;
             }
         }
-        lSx += 1.5 * lsrc + lS_in[n];
-        lS_out[n] = -0.5 * lsrc;
+        lSx += R(1.5) * lsrc + lS_in[n];
+        lS_out[n] = R(-0.5) * lsrc;
 
         // NS collision
-        double lgn[9];
+        R lgn[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) lgn[i] = 0.0;
+        for (int i = 0; i < 9; ++i) lgn[i] = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double l = lg_in[i * N + at(geo, x, y, cxa(i), cya(i))];
-            const double cF = cxa(i) * F[0] + cya(i) * F[1];
-            const double cu = cxa(i) * u[0] + cya(i) * u[1];
-            const double cg = cxa(i) * gr[0] + cya(i) * gr[1];
-            const double gam = wa(i) * (ugr + cF / CS2A + (cu * cg - CS2A * ugr) / CS2A);
-            const double ge = p / CS2A * (wa(i) - (i == 0 ? 1.0 : 0.0)) +
-                              rho * wa(i) * (cu / CS2A + cu * cu / (2 * CS2A * CS2A) - uu / (2 * CS2A));
-            lgn[i] += (1.0 - itg) * l;
-            litg += l * (ge - gv[i]) - 0.5 * l * gam;
-            const double lge = l * itg, lgam = l * (1.0 - 0.5 * itg);
-            lp += lge * (wa(i) - (i == 0 ? 1.0 : 0.0)) / CS2A;
-            lrho += lge * wa(i) * (cu / CS2A + cu * cu / (2 * CS2A * CS2A) - uu / (2 * CS2A));
+            const R l = lg_in[i * N + at(geo, x, y, cxa(i), cya(i))];
+            const R w = R(wa(i));
+            const R cF = R(cxa(i)) * F[0] + R(cya(i)) * F[1];
+            const R cu = R(cxa(i)) * u[0] + R(cya(i)) * u[1];
+            const R cg = R(cxa(i)) * gr[0] + R(cya(i)) * gr[1];
+            const R gam = w * (ugr + cF * IC + (cu * cg - R(CS2A) * ugr) * IC);
+            const R su = cu * IC + cu * cu * R(0.5 / (CS2A * CS2A)) - uu * R(0.5 / CS2A);
+            const R ge = p * R((wa(i) - (i == 0 ? 1.0 : 0.0)) / CS2A) + rho * w * su;
+            lgn[i] += (R(1) - itg) * l;
+            litg += l * (ge - gv[i]) - R(0.5) * l * gam;
+            const R lge = l * itg, lgam = l * (R(1) - R(0.5) * itg);
+            lp += lge * R((wa(i) - (i == 0 ? 1.0 : 0.0)) / CS2A);
+            lrho += lge * w * su;
             const int c[2] = {cxa(i), cya(i)};
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                lu[a] += lge * rho * wa(i) * (c[a] / CS2A + cu * c[a] / (CS2A * CS2A) - u[a] / CS2A);
-                lF[a] += lgam * wa(i) * c[a] / CS2A;
-                lu[a] += lgam * wa(i) * (gr[a] + (c[a] * cg - CS2A * gr[a]) / CS2A);
-                lgr[a] += lgam * wa(i) * (u[a] + (cu * c[a] - CS2A * u[a]) / CS2A);
+                lu[a] += lge * rho * w * (R(c[a]) * IC + cu * R(c[a]) * IC * IC - u[a] * IC);
+                lF[a] += lgam * w * R(c[a]) * IC;
+                lu[a] += lgam * w * (gr[a] + (R(c[a]) * cg - R(CS2A) * gr[a]) * IC);
+                lgr[a] += lgam * w * (u[a] + (cu * R(c[a]) - R(CS2A) * u[a]) * IC);
             }
         }
-        lph += litg * (-(dnu / CS2A) * itg * itg);  // tau_g = 1/2 + nu(phi)/cs2
+        lph += litg * (-(dnu * IC) * itg * itg);  // tau_g = 1/2 + nu(phi)/cs2
         // S = u.grad phi
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
@@ -169,26 +186,27 @@ __global__ void adj_local(const StepParams<double> P, AdjGeom geo, const T *__re
         }
         // p = cs2/(1-w0) [sum_{i!=0} g_i + u.grad rho/2 - rho w0 uu/(2 cs2)]
         {
-            const double k = CS2A / (1.0 - wa(0));
+            const R k = R(CS2A / (1.0 - wa(0)));
 #pragma unroll
             for (int i = 1; i < 9; ++i) lgn[i] += k * lp;
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                lu[a] += k * lp * (0.5 * gr[a] - rho * wa(0) * u[a] / CS2A);
-                lgr[a] += k * lp * 0.5 * u[a];
+                lu[a] += k * lp * (R(0.5) * gr[a] - rho * R(wa(0)) * u[a] * IC);
+                lgr[a] += k * lp * R(0.5) * u[a];
             }
-            lrho += k * lp * (-wa(0) * uu / (2 * CS2A));
+            lrho += k * lp * (-R(wa(0) / (2 * CS2A)) * uu);
         }
 #pragma unroll
         for (int a = 0; a < 2; ++a) lgp[a] += drho * lgr[a];
         // u = (sum c g + F/2) / rho
+        const R irho = R(1) / rho;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            const double lj = lu[a] / rho;
+            const R lj = lu[a] * irho;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) lgn[i] += (a == 0 ? cxa(i) : cya(i)) * lj;
-            lF[a] += 0.5 * lj;
-            lrho += -lu[a] * u[a] / rho;
+            for (int i = 0; i < 9; ++i) lgn[i] += R(a == 0 ? cxa(i) : cya(i)) * lj;
+            lF[a] += R(0.5) * lj;
+            lrho += -lu[a] * u[a] * irho;
         }
         // F = -phi grad mu + G
 #pragma unroll
@@ -203,35 +221,37 @@ __global__ void adj_local(const StepParams<double> P, AdjGeom geo, const T *__re
         lphi[n] = lph;
         lmu[n] = lmux;
     }
-    // dL/d(1/tau_f): warp sum, one FP64 atomic per warp
-    for (int o = 16; o > 0; o >>= 1) itf_part += __shfl_xor_sync(0xffffffffu, itf_part, o);
-    if ((threadIdx.x & 31) == 0 && itf_part != 0.0) atomicAdd(dpar + 2, itf_part);
+    // dL/d(1/tau_f): one FP64 atomic per block
+    block_add((double)itf_part, dpar + 2);
 }
 
 // transpose of the gradient stencil: (G^T v)(y) = (1/cs2) sum_i w_i c_i . v(y - c_i)
-__device__ __forceinline__ double gradT_at(const AdjGeom &g, const double *v, int x, int y)
+template <typename R>
+__device__ __forceinline__ R gradT_at(const AdjGeom &g, const R *v, int x, int y)
 {
-    double s = 0.0;
+    R s = R(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const unsigned m = at(g, x, y, -cxa(i), -cya(i));
-        s += wa(i) * (cxa(i) * v[m] + cya(i) * v[g.N + m]);
+        s += R(wa(i) / CS2A) * (R(cxa(i)) * v[m] + R(cya(i)) * v[g.N + m]);
     }
-    return s / CS2A;
+    return s;
 }
 
-// symmetric Laplacian: (L v)(x) = (2/cs2) sum_i w_i (v(x + c_i) - v(x))
-__device__ __forceinline__ double lap_at(const AdjGeom &g, const double *v, int x, int y)
+// symmetric Laplacian: (L v)(x) = (2/cs2) sum_i w_i (v(x + c_i) - v(x)), in R
+template <typename R, typename V>
+__device__ __forceinline__ R lap_at(const AdjGeom &g, const V *v, int x, int y)
 {
-    const double c = v[(unsigned)y * g.nx + x];
-    double s = 0.0;
+    const R c = (R)v[(unsigned)y * g.nx + x];
+    R s = R(0);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) s += 2.0 * wa(i) * (v[at(g, x, y, cxa(i), cya(i))] - c);
-    return s / CS2A;
+    for (int i = 1; i < 9; ++i) s += R(2.0 * wa(i) / CS2A) * ((R)v[at(g, x, y, cxa(i), cya(i))] - c);
+    return s;
 }
 
-__global__ void adj_mu(AdjGeom geo, const double *__restrict__ lmu, const double *__restrict__ lgmu,
-                       double *__restrict__ lmu_tot)
+template <typename R>
+__global__ void adj_mu(AdjGeom geo, const R *__restrict__ lmu, const R *__restrict__ lgmu,
+                       R *__restrict__ lmu_tot)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= geo.N) return;
@@ -240,115 +260,141 @@ __global__ void adj_mu(AdjGeom geo, const double *__restrict__ lmu, const double
 }
 
 // lambda_phi total; lambda_f += lambda_phi for every i; dL/dkappa, dL/dbeta
+template <typename R>
 __global__ void adj_phi(const StepParams<double> P, AdjGeom geo, const double *__restrict__ phi,
-                        const double *__restrict__ lphi, const double *__restrict__ lgphi,
-                        const double *__restrict__ lmu_tot, double *__restrict__ lf_out,
-                        double *lphi_out, double *dpar)
+                        const R *__restrict__ lphi, const R *__restrict__ lgphi,
+                        const R *__restrict__ lmu_tot, R *__restrict__ lf_out, double *lphi_out,
+                        double *dpar)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
-    double dk = 0.0, db = 0.0;
+    R dk = R(0), db = R(0);
     if (n < geo.N) {
         const int x = n % geo.nx, y = n / geo.nx;
-        const double ph = phi[n], lm = lmu_tot[n];
-        const double a = ph - P.phil, b = ph - P.phiv, c = ph - P.phibar;
-        const double d2psi = 4.0 * P.beta * (b * c + a * c + a * b);
-        double l = lphi[n] + gradT_at(geo, lgphi, x, y) + d2psi * lm - P.kappa * lap_at(geo, lmu_tot, x, y);
-        dk = lm * (-lap_at(geo, phi, x, y));
-        db = lm * 4.0 * a * b * c;
+        const R ph = (R)phi[n], lm = lmu_tot[n];
+        const R a = ph - (R)P.phil, b = ph - (R)P.phiv, c = ph - (R)P.phibar;
+        const R d2psi = R(4) * (R)P.beta * (b * c + a * c + a * b);
+        const R l = lphi[n] + gradT_at(geo, lgphi, x, y) + d2psi * lm -
+                    (R)P.kappa * lap_at<R>(geo, lmu_tot, x, y);
+        dk = lm * (-lap_at<R>(geo, phi, x, y));
+        db = lm * R(4) * a * b * c;
         if (lf_out) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) lf_out[i * geo.N + n] += l;
         }
-        if (lphi_out) lphi_out[n] = l;
+        if (lphi_out) lphi_out[n] = (double)l;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        dk += __shfl_xor_sync(0xffffffffu, dk, o);
-        db += __shfl_xor_sync(0xffffffffu, db, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (dk != 0.0) atomicAdd(dpar + 0, dk);
-        if (db != 0.0) atomicAdd(dpar + 1, db);
-    }
+    block_add((double)dk, dpar + 0);
+    block_add((double)db, dpar + 1);
 }
 
 // initial condition f = f^eq(phi0, mu(phi0)): lambda_phi and lambda_mu from lambda_f
-__global__ void adj_init_local(const StepParams<double> P, AdjGeom geo, const double *__restrict__ lf,
-                               double *__restrict__ lphi, double *__restrict__ lmu,
-                               double *__restrict__ lgphi)
+template <typename R>
+__global__ void adj_init_local(const StepParams<double> P, AdjGeom geo, const R *__restrict__ lf,
+                               R *__restrict__ lphi, R *__restrict__ lmu, R *__restrict__ lgphi)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= geo.N) return;
-    double l = -(1.0 - wa(0)) * P.alpha * lf[n];
+    const R alpha = (R)P.alpha;
+    R l = -R(1.0 - wa(0)) * alpha * lf[n];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) l += wa(i) * P.alpha * lf[i * geo.N + n];
+    for (int i = 1; i < 9; ++i) l += R(wa(i)) * alpha * lf[i * geo.N + n];
     lmu[n] = l;
     lphi[n] = lf[n];
-    lgphi[n] = 0.0;
-    lgphi[geo.N + n] = 0.0;
+    lgphi[n] = R(0);
+    lgphi[geo.N + n] = R(0);
 }
 
 // adjoint of the final state for L(phi^N): lambda_f_i = dL/dphi for every i
-__global__ void adj_seed(unsigned N, const double *__restrict__ dphi, double *__restrict__ lf,
-                         double *__restrict__ lg, double *__restrict__ lS)
+template <typename R>
+__global__ void adj_seed(unsigned N, const double *__restrict__ dphi, R *__restrict__ lf,
+                         R *__restrict__ lg, R *__restrict__ lS)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const double v = dphi[n];
+    const R v = (R)dphi[n];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         lf[i * N + n] = v;
-        lg[i * N + n] = 0.0;
+        lg[i * N + n] = R(0);
     }
-    lS[n] = 0.0;
+    lS[n] = R(0);
+}
+
+template <typename R>
+void adj_step_t(int precision, const StepParams<double> &P, AdjGeom geo, const void *f,
+                const void *g, const double *phi, const double *mu, const double *p,
+                const double *u, const R *lf_in, const R *lg_in, const R *lS_in, R *lf_out,
+                R *lg_out, R *lS_out, R *work, double *dpar, cudaStream_t st)
+{
+    const unsigned N = geo.N;
+    R *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N, *lgmu = work + 4 * (size_t)N,
+      *lmu_tot = work + 6 * (size_t)N;
+    const unsigned nb = (N + 255) / 256;
+    if (precision == 0)
+        adj_local<double, R><<<nb, 256, 0, st>>>(P, geo, (const double *)f, (const double *)g, 0,
+                                                 phi, mu, p, u, lf_in, lg_in, lS_in, lf_out,
+                                                 lg_out, lS_out, lphi, lmu, lgphi, lgmu, dpar);
+    else
+        adj_local<float, R><<<nb, 256, 0, st>>>(P, geo, (const float *)f, (const float *)g, 1, phi,
+                                                mu, p, u, lf_in, lg_in, lS_in, lf_out, lg_out,
+                                                lS_out, lphi, lmu, lgphi, lgmu, dpar);
+    adj_mu<R><<<nb, 256, 0, st>>>(geo, lmu, lgmu, lmu_tot);
+    adj_phi<R><<<nb, 256, 0, st>>>(P, geo, phi, lphi, lgphi, lmu_tot, lf_out, nullptr, dpar);
+}
+
+template <typename R>
+void adj_init_t(const StepParams<double> &P, AdjGeom geo, const double *phi0, const R *lf,
+                R *work, double *lphi0, double *dpar, cudaStream_t st)
+{
+    const unsigned N = geo.N;
+    R *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N;
+    const unsigned nb = (N + 255) / 256;
+    adj_init_local<R><<<nb, 256, 0, st>>>(P, geo, lf, lphi, lmu, lgphi);
+    adj_phi<R><<<nb, 256, 0, st>>>(P, geo, phi0, lphi, lgphi, lmu, nullptr, lphi0, dpar);
 }
 
 }  // namespace
 
-cudaError_t adj_d2q9_seed(int N, const double *dphi, double *lf, double *lg, double *lS,
+cudaError_t adj_d2q9_seed(int real, int N, const double *dphi, void *lf, void *lg, void *lS,
                           cudaStream_t st)
 {
-    adj_seed<<<(N + 255) / 256, 256, 0, st>>>((unsigned)N, dphi, lf, lg, lS);
+    if (real == 0)
+        adj_seed<double><<<(N + 255) / 256, 256, 0, st>>>((unsigned)N, dphi, (double *)lf,
+                                                          (double *)lg, (double *)lS);
+    else
+        adj_seed<float><<<(N + 255) / 256, 256, 0, st>>>((unsigned)N, dphi, (float *)lf,
+                                                         (float *)lg, (float *)lS);
     return cudaGetLastError();
 }
 
 cudaError_t adj_d2q9_step(int precision, const void *params64, int nx, int ny, const void *f,
-                          const void *g, const void *S, const double *phi, const double *mu,
-                          const double *p, const double *u, const double *lf_in,
-                          const double *lg_in, const double *lS_in, double *lf_out, double *lg_out,
-                          double *lS_out, double *work, double *dpar, cudaStream_t st)
-{
-    const StepParams<double> &P = *static_cast<const StepParams<double> *>(params64);
-    AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
-    const unsigned N = geo.N;
-    double *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N,
-           *lgmu = work + 4 * (size_t)N, *lmu_tot = work + 6 * (size_t)N;
-    const unsigned nb = (N + 255) / 256;
-    if (precision == 0)
-        adj_local<double><<<nb, 256, 0, st>>>(P, geo, (const double *)f, (const double *)g,
-                                              (const double *)S, 0, phi, mu, p, u, lf_in, lg_in,
-                                              lS_in, lf_out, lg_out, lS_out, lphi, lmu, lgphi,
-                                              lgmu, dpar);
-    else
-        adj_local<float><<<nb, 256, 0, st>>>(P, geo, (const float *)f, (const float *)g,
-                                             (const float *)S, 1, phi, mu, p, u, lf_in, lg_in,
-                                             lS_in, lf_out, lg_out, lS_out, lphi, lmu, lgphi,
-                                             lgmu, dpar);
-    adj_mu<<<nb, 256, 0, st>>>(geo, lmu, lgmu, lmu_tot);
-    adj_phi<<<nb, 256, 0, st>>>(P, geo, phi, lphi, lgphi, lmu_tot, lf_out, nullptr, dpar);
-    return cudaGetLastError();
-}
-
-cudaError_t adj_d2q9_init(const void *params64, int nx, int ny, const double *phi0,
-                          const double *lf, double *work, double *lphi0, double *dpar,
+                          const void *g, const double *phi, const double *mu, const double *p,
+                          const double *u, const void *lf_in, const void *lg_in, const void *lS_in,
+                          void *lf_out, void *lg_out, void *lS_out, void *work, double *dpar,
                           cudaStream_t st)
 {
     const StepParams<double> &P = *static_cast<const StepParams<double> *>(params64);
-    AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
-    const unsigned N = geo.N;
-    double *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N;
-    const unsigned nb = (N + 255) / 256;
-    adj_init_local<<<nb, 256, 0, st>>>(P, geo, lf, lphi, lmu, lgphi);
-    adj_phi<<<nb, 256, 0, st>>>(P, geo, phi0, lphi, lgphi, lmu, nullptr, lphi0, dpar);
+    const AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
+    if (precision == 0)
+        adj_step_t<double>(0, P, geo, f, g, phi, mu, p, u, (const double *)lf_in,
+                           (const double *)lg_in, (const double *)lS_in, (double *)lf_out,
+                           (double *)lg_out, (double *)lS_out, (double *)work, dpar, st);
+    else
+        adj_step_t<float>(1, P, geo, f, g, phi, mu, p, u, (const float *)lf_in,
+                          (const float *)lg_in, (const float *)lS_in, (float *)lf_out,
+                          (float *)lg_out, (float *)lS_out, (float *)work, dpar, st);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_d2q9_init(int real, const void *params64, int nx, int ny, const double *phi0,
+                          const void *lf, void *work, double *lphi0, double *dpar, cudaStream_t st)
+{
+    const StepParams<double> &P = *static_cast<const StepParams<double> *>(params64);
+    const AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
+    if (real == 0)
+        adj_init_t<double>(P, geo, phi0, (const double *)lf, (double *)work, lphi0, dpar, st);
+    else
+        adj_init_t<float>(P, geo, phi0, (const float *)lf, (float *)work, lphi0, dpar, st);
     return cudaGetLastError();
 }
 

@@ -210,21 +210,22 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     const int nout = yend - y0;
     auto slot = [&](int row) { return (dir * (row - first) + 2) % R; };
 
+    // phi = f_0 + rest into ring slot sl, column j
+    auto put_phi = [&](int sl, int j, T f0, T rest) { phs[sl * WP + j] = f0 + rest; };
     // phi at row `row` for the own column (keeping the pulled values) and the
     // halo columns.
     auto phi_row = [&](int row, int sl, T v[9], T &lo) {
         const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
         const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
         const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
-        T *ph = phs + sl * WP;
         pull9(fsrc, N, rm, r0, rp, xOm, xO, xOp, v);
         lo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xO)) : T(0);
-        ph[tx + 2] = v[0] + (lo + sum_moving(v));
+        put_phi(sl, tx + 2, v[0], lo + sum_moving(v));
         if (tx < 4) {
             T h[9];
             pull9(fsrc, N, rm, r0, rp, xHm, xH, xHp, h);
             const T hlo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xH)) : T(0);
-            ph[jH] = h[0] + (hlo + sum_moving(h));
+            put_phi(sl, jH, h[0], hlo + sum_moving(h));
         }
     };
 
@@ -244,27 +245,27 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     };
     // phi row from stage st (the copies have landed)
     auto phi_row_staged = [&](int sl, int st, T v[9], T &lo) {
-        T *ph = phs + sl * WP;
         const T *d = fst + (size_t)st * NFS * NT + lin;
 #pragma unroll
         for (int i = 0; i < 9; ++i) v[i] = d[i * NT];
         lo = REST_PAIR ? d[9 * NT] : T(0);
-        ph[tx + 2] = v[0] + (lo + sum_moving(v));
+        put_phi(sl, tx + 2, v[0], lo + sum_moving(v));
         if (tx < 4) {
             const T *h = fsh + (size_t)st * NFS * 4 * TYB + ty * 4 + tx;
             T hv[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) hv[i] = h[i * 4 * TYB];
             const T hlo = REST_PAIR ? h[9 * 4 * TYB] : T(0);
-            ph[jH] = hv[0] + (hlo + sum_moving(hv));
+            put_phi(sl, jH, hv[0], hlo + sum_moving(hv));
         }
     };
 
     // Eq. chemical_potencial with the Laplacian of Eq. Laplace, written as a
     // sum of differences (cancellation-friendly in FP32):
     // lap = (2/3) sum_axis (phi_n - phi) + (1/6) sum_diag (phi_n - phi).
-    auto mu_at = [&](const T *pm, const T *p0, const T *pp, int j) -> T {
+    auto mu_at = [&](int sm, int s0, int sp, int j) -> T {
         // j is the mu ring index; the phi ring index of the same column is j+1
+        const T *pm = phs + sm * WP, *p0 = phs + s0 * WP, *pp = phs + sp * WP;
         const T c = p0[j + 1];
         const T ax = (p0[j + 2] - c) + (p0[j] - c) + (pp[j + 1] - c) + (pm[j + 1] - c);
         const T dg = (pp[j + 2] - c) + (pp[j] - c) + (pm[j + 2] - c) + (pm[j] - c);
@@ -274,12 +275,9 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     };
     // mu at the row with ring slot s0; sm / sp are the slots of rows y-1 / y+1
     auto mu_row = [&](int sm, int s0, int sp) {
-        const T *pm = phs + sm * WP;
-        const T *p0 = phs + s0 * WP;
-        const T *pp = phs + sp * WP;
         T *mr = mus + s0 * WM;
-        mr[tx + 1] = mu_at(pm, p0, pp, tx + 1);
-        if (tx < 2) mr[jM] = mu_at(pm, p0, pp, jM);
+        mr[tx + 1] = mu_at(sm, s0, sp, tx + 1);
+        if (tx < 2) mr[jM] = mu_at(sm, s0, sp, jM);
     };
 
     double d_phi = 0.0, d_E = 0.0, d_u2 = 0.0, d_mumin = DBL_MAX, d_mumax = -DBL_MAX,
@@ -414,12 +412,16 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
                 st_stream(static_cast<T *>(a.S_out) + n, S);
 
                 // CH population, Eq. BGK with Eq. H_i and Eq. F_i:
-                // f* = f (1 - 1/tau_f) + f^eq/tau_f + w_i b_i (1.5 S - 0.5 S_prev),
+                // f* = f - (f - f^eq)/tau_f + w_i b_i (1.5 S - 0.5 S_prev),
                 // b = -2, -1/2, 1 (rest, axis, diagonal); f_0 - f_0^eq is formed
                 // as (5/9) alpha mu - sum_{i!=0} f_i (no cancellation against phi).
+                // Every population is updated by its own small increment, so
+                // the increments sum to sum_i F_i up to unbiased rounding (the
+                // form f (1 - 1/tau) + f^eq/tau would add (1 - 1/tau + 1/tau - 1)
+                // sum_{i!=0} f_i, a systematic FP32 drift of the phi mass).
                 const T Sh = T(1.5) * S - T(0.5) * Sprev;
                 const T am = P.alpha * mu;
-                const T itf = P.inv_tauf, omf = T(1) - itf;
+                const T itf = P.inv_tauf;
                 {
                     // f_0* = f_0 - (f_0 - f_0^eq)/tau_f - (8/9) Sh with
                     // f_0 - f_0^eq = (5/9) alpha mu - sum_{i!=0} f_i
@@ -436,24 +438,26 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
                         st_stream(fd + n, fcur[0] + d0);
                     }
                 }
-                const T ka = (T(1.0 / 9.0) * am) * itf - T(1.0 / 18.0) * Sh;
-                const T kd = (T(1.0 / 36.0) * am) * itf + T(1.0 / 36.0) * Sh;
+                const T ea = T(1.0 / 9.0) * am, ed = T(1.0 / 36.0) * am;
+                const T sa = T(-1.0 / 18.0) * Sh, sd = T(1.0 / 36.0) * Sh;
 #pragma unroll
-                for (int i = 1; i <= 4; ++i) st_stream(fd + (i * N + n), fcur[i] * omf + ka);
+                for (int i = 1; i <= 4; ++i)
+                    st_stream(fd + (i * N + n), fcur[i] + ((ea - fcur[i]) * itf + sa));
 #pragma unroll
-                for (int i = 5; i <= 8; ++i) st_stream(fd + (i * N + n), fcur[i] * omf + kd);
+                for (int i = 5; i <= 8; ++i)
+                    st_stream(fd + (i * N + n), fcur[i] + ((ed - fcur[i]) * itf + sd));
 
                 // Hydrodynamic population, Eq. BGK-NS with Eqs. G_i, Siu, GGi:
-                // g* = g (1 - 1/tau_g) + g^eq/tau_g + G_i.  With A = 3p - 1.5 rho |u|^2,
+                // g* = g + (g^eq - g)/tau_g + G_i.  With A = 3p - 1.5 rho |u|^2,
                 // g^eq_i = w_i [A + 4.5 rho (c.u)^2] + 3 w_i rho (c.u) (i != 0), and
                 // G_i = (1 - 1/(2 tau_g)) w_i [u.grad rho + c.F/cs2
                 //       + ((c.u)(c.grad rho) - cs2 u.grad rho)/cs2]
                 //     = 3 w_i k [c.F + (c.u)(c.grad rho)], k = 1 - 1/(2 tau_g)
                 // (the two u.grad rho terms cancel).  Opposite directions share
                 // the even part and flip the odd part.
-                const T kg = T(1) - T(0.5) * itg, omg = T(1) - itg;
+                const T kg = T(1) - T(0.5) * itg;
                 const T A = T(3) * p - T(1.5) * rho * uu;
-                st_stream(gd + n, gv[0] * omg + (T(4.0 / 9.0) * A - T(3) * p) * itg);  // G_0 = 0
+                st_stream(gd + n, gv[0] + ((T(4.0 / 9.0) * A - T(3) * p) - gv[0]) * itg);  // G_0 = 0
                 const T cu_[4] = {ux, uy, ux + uy, uy - ux};
                 const T cF_[4] = {Fx, Fy, Fx + Fy, Fy - Fx};
                 const T cg_[4] = {grx, gry, grx + gry, gry - grx};
@@ -462,10 +466,11 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
                 for (int q = 0; q < 4; ++q) {
                     const T w = q < 2 ? T(1.0 / 9.0) : T(1.0 / 36.0);
                     const T cu = cu_[q];
-                    const T sym = w * ((A + T(4.5) * rho * cu * cu) * itg + T(3) * kg * cu * cg_[q]);
-                    const T asym = T(3) * w * (rho * cu * itg + kg * cF_[q]);
-                    st_stream(gd + (ip[q] * N + n), gv[ip[q]] * omg + sym + asym);
-                    st_stream(gd + (im[q] * N + n), gv[im[q]] * omg + sym - asym);
+                    const T eq_s = w * (A + T(4.5) * rho * cu * cu), eq_a = T(3) * w * rho * cu;
+                    const T G_s = T(3) * w * kg * cu * cg_[q], G_a = T(3) * w * kg * cF_[q];
+                    const T gp = gv[ip[q]], gm = gv[im[q]];
+                    st_stream(gd + (ip[q] * N + n), gp + ((eq_s + eq_a - gp) * itg + (G_s + G_a)));
+                    st_stream(gd + (im[q] * N + n), gm + ((eq_s - eq_a - gm) * itg + (G_s - G_a)));
                 }
             }
         }
@@ -684,10 +689,12 @@ LaunchShape d2q9_shape(int nx, int ny, int num_sms)
     s.variant = TXW;
     s.grid_x = (nx + TXW - 1) / TXW;
     // one wave of resident CTAs (4 per SM at the FP32 register budget) when
-    // the grid allows it; rows even (two rows per iteration), at least 8
+    // the grid allows it; rows even (two rows per iteration).  Small grids
+    // get short marches (down to one iteration) so that more CTAs share the
+    // latency of a step.
     const long long slots = 4LL * (num_sms > 0 ? num_sms : 152);
     long long rows = ((long long)s.grid_x * ny + slots - 1) / slots;
-    if (rows < 8) rows = 8;
+    if (rows < 2) rows = 2;
     if (rows > 256) rows = 256;
     rows += rows & 1;
     s.rows = (int)rows;

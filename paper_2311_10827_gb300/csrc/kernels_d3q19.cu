@@ -16,66 +16,13 @@
 #include <float.h>
 #include <math.h>
 
+#include "d3q19_lattice.cuh"
 #include "lbm_internal.h"
 
 namespace wblbm {
 namespace {
 
-// velocity order: rest; +x, -x, +y, -y, +z, -z; then the 12 edges
-// (+x+y, +x-y, -x+y, -x-y), (+x+z, +x-z, -x+z, -x-z), (+y+z, +y-z, -y+z, -y-z)
-__host__ __device__ constexpr int c3x(int i)
-{
-    return (i == 1 || i == 7 || i == 8 || i == 11 || i == 12)
-               ? 1
-               : ((i == 2 || i == 9 || i == 10 || i == 13 || i == 14) ? -1 : 0);
-}
-__host__ __device__ constexpr int c3y(int i)
-{
-    return (i == 3 || i == 7 || i == 9 || i == 15 || i == 16)
-               ? 1
-               : ((i == 4 || i == 8 || i == 10 || i == 17 || i == 18) ? -1 : 0);
-}
-__host__ __device__ constexpr int c3z(int i)
-{
-    return (i == 5 || i == 11 || i == 13 || i == 15 || i == 17)
-               ? 1
-               : ((i == 6 || i == 12 || i == 14 || i == 16 || i == 18) ? -1 : 0);
-}
-__host__ __device__ constexpr double w3(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
-__device__ __forceinline__ int wrapi(int c, int n)
-{
-    int r = c % n;
-    return r < 0 ? r + n : r;
-}
-
-template <typename T>
-struct Arith3;
-template <>
-struct Arith3<float> {
-    __device__ static float rcp(float x) { return __fdividef(1.0f, x); }
-};
-template <>
-struct Arith3<double> {
-    __device__ static double rcp(double x) { return 1.0 / x; }
-};
-
-// offsets of the 27 neighbours (dx, dy, dz in -1..1) of a node from wrapped
-// coordinates
-struct Nb {
-    unsigned xs[3], ys[3], zs[3];  // x-1, x, x+1 etc. (already multiplied: y*nx, z*nx*ny)
-    __device__ unsigned at(int dx, int dy, int dz) const { return zs[dz + 1] + ys[dy + 1] + xs[dx + 1]; }
-};
-
-__device__ __forceinline__ Nb make_nb(int x, int y, int z, int nx, int ny, int nz)
-{
-    Nb b;
-    for (int d = -1; d <= 1; ++d) {
-        b.xs[d + 1] = (unsigned)wrapi(x + d, nx);
-        b.ys[d + 1] = (unsigned)wrapi(y + d, ny) * nx;
-        b.zs[d + 1] = (unsigned)wrapi(z + d, nz) * nx * ny;
-    }
-    return b;
-}
+using namespace d3;
 
 // phi = sum_i f_i(x - c_i): rest population last, moving ones in fixed pairs
 template <typename T>
@@ -95,8 +42,6 @@ __global__ void d3q19_phi_kernel(const StepParams<T> P, const T *__restrict__ f,
     for (int i = 1; i < 19; i += 2) s += v[i] + v[i + 1];
     phi[n] = v[0] + s;
 }
-
-constexpr int TX3 = 32, TY3 = 8;
 
 template <typename T, int PASS>
 __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T> P, PassArgs a,
@@ -167,20 +112,33 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
     double d_phi = 0.0, d_E = 0.0, d_u2 = 0.0, d_mumin = DBL_MAX, d_mumax = -DBL_MAX,
            d_bud = 0.0, d_bad = 0.0;
 
-    for (int q = 0; q < 4; ++q) load_phi_plane(z0 - 2 + q);
+    for (int q = 0; q < 5; ++q) load_phi_plane(z0 - 2 + q);
     __syncthreads();
     mu_plane(z0 - 1);
     mu_plane(z0);
+    mu_plane(z0 + 1);
     __syncthreads();
 
+    // Plane zz + 3 of phi travels through registers while plane zz is
+    // updated, so its loads overlap the node's own pulls (one exposed memory
+    // latency per plane).  Ring use during the update of plane zz: phi planes
+    // zz-1..zz+1 (read), zz+3 (written: a fifth slot); mu planes zz-1..zz+1.
+    constexpr int PPT = (PA + TX3 * TY3 - 1) / (TX3 * TY3);
     const unsigned xw = col_ok ? (unsigned)x : 0, yw = col_ok ? (unsigned)y : 0;
     for (int zz = z0; zz < zend; ++zz) {
-        load_phi_plane(zz + 2);
-        __syncthreads();
-        mu_plane(zz + 1);
-        __syncthreads();
-        if (!col_ok) continue;
-
+        T pre[PPT];
+        {
+            const unsigned zo = (unsigned)wrapi(zz + 3, nz) * plane;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int q = tid + k * TX3 * TY3;
+                if (q < PA) {
+                    const unsigned xx = wrapi(x0 - 2 + q % PX, nx), yy = wrapi(y0 - 2 + q / PX, ny);
+                    pre[k] = phif[zo + yy * nx + xx];
+                }
+            }
+        }
+        if (col_ok) {
         const Nb b = make_nb(xw, yw, zz, nx, ny, nz);
         const unsigned n = b.at(0, 0, 0);
         T fv[19], gv[19];
@@ -264,7 +222,7 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
             // CH population: b = -5/2, -1, 1/2 (rest, face, edge) for D = 3
             const T Sh = T(1.5) * S - T(0.5) * Sprev;
             const T am = P.alpha * mu;
-            const T itf = P.inv_tauf, omf = T(1) - itf;
+            const T itf = P.inv_tauf;
             {
                 const T d0 = -(T(2.0 / 3.0) * am - snz) * itf - T(5.0 / 6.0) * Sh;
                 if (sizeof(T) == 4) {
@@ -277,14 +235,17 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
                     __stcs(fd + n, fv[0] + d0);
                 }
             }
-            const T ka = (T(1.0 / 18.0) * am) * itf - T(1.0 / 18.0) * Sh;
-            const T ke = (T(1.0 / 36.0) * am) * itf + T(1.0 / 72.0) * Sh;
+            // each population moves by its own small increment (as in 2D: the
+            // increments sum to sum_i F_i up to unbiased rounding)
+            const T ea = T(1.0 / 18.0) * am, ee = T(1.0 / 36.0) * am;
+            const T sa = T(-1.0 / 18.0) * Sh, se = T(1.0 / 72.0) * Sh;
 #pragma unroll
-            for (int i = 1; i < 19; ++i) __stcs(fd + (i * N + n), fv[i] * omf + (i <= 6 ? ka : ke));
+            for (int i = 1; i < 19; ++i)
+                __stcs(fd + (i * N + n), fv[i] + (((i <= 6 ? ea : ee) - fv[i]) * itf + (i <= 6 ? sa : se)));
             // hydrodynamic population, pairs of opposite directions (as in 2D)
-            const T kg = T(1) - T(0.5) * itg, omg = T(1) - itg;
+            const T kg = T(1) - T(0.5) * itg;
             const T A = T(3) * p - T(1.5) * rho * uu;
-            __stcs(gd + n, gv[0] * omg + (T(1.0 / 3.0) * A - T(3) * p) * itg);
+            __stcs(gd + n, gv[0] + ((T(1.0 / 3.0) * A - T(3) * p) - gv[0]) * itg);
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
                 const int o = (i <= 6) ? (i % 2 ? i + 1 : i - 1) : (i <= 10 ? 17 - i : (i <= 14 ? 25 - i : 33 - i));
@@ -293,12 +254,24 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
                 const T cu = T(c3x(i)) * u[0] + T(c3y(i)) * u[1] + T(c3z(i)) * u[2];
                 const T cF = T(c3x(i)) * F[0] + T(c3y(i)) * F[1] + T(c3z(i)) * F[2];
                 const T cg = T(c3x(i)) * gr[0] + T(c3y(i)) * gr[1] + T(c3z(i)) * gr[2];
-                const T sym = w * ((A + T(4.5) * rho * cu * cu) * itg + T(3) * kg * cu * cg);
-                const T asym = T(3) * w * (rho * cu * itg + kg * cF);
-                __stcs(gd + (i * N + n), gv[i] * omg + sym + asym);
-                __stcs(gd + (o * N + n), gv[o] * omg + sym - asym);
+                const T eq_s = w * (A + T(4.5) * rho * cu * cu), eq_a = T(3) * w * rho * cu;
+                const T G_s = T(3) * w * kg * cu * cg, G_a = T(3) * w * kg * cF;
+                __stcs(gd + (i * N + n), gv[i] + ((eq_s + eq_a - gv[i]) * itg + (G_s + G_a)));
+                __stcs(gd + (o * N + n), gv[o] + ((eq_s - eq_a - gv[o]) * itg + (G_s - G_a)));
             }
         }
+        }  // col_ok
+        {
+            T *d = phs + pslot(zz + 3) * PA;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int q = tid + k * TX3 * TY3;
+                if (q < PA) d[q] = pre[k];
+            }
+        }
+        __syncthreads();
+        mu_plane(zz + 2);
+        __syncthreads();
     }
 
     if (PASS & PASS_DIAG) {
@@ -455,21 +428,44 @@ cudaError_t pass3_t(int pass, const void *params, const PassArgs &a, const Launc
 
 }  // namespace
 
-LaunchShape d3q19_shape(int nx, int ny, int nz, int num_sms)
+LaunchShape d3q19_shape(int nx, int ny, int nz, int num_sms, int ctas_per_sm)
 {
     LaunchShape s;
     s.variant = 0;
     s.grid_x = (nx + TX3 - 1) / TX3;
     s.grid_y = (ny + TY3 - 1) / TY3;
-    // planes per CTA: about 4 CTAs per SM in one wave, marching >= 4 planes
-    const long long slots = 4LL * (num_sms > 0 ? num_sms : 152);
-    long long planes = ((long long)s.grid_x * s.grid_y * nz + slots - 1) / slots;
-    if (planes < 4) planes = 4;
-    if (planes > nz) planes = nz;
-    s.rows = (int)planes;
-    const int gz = (int)((nz + planes - 1) / planes);
-    s.nblocks = s.grid_x * s.grid_y * gz;
+    // Split z into gz marches of `planes` planes.  Time ~ waves x (planes + 2)
+    // (a march starts by filling its rings, about two planes of work), waves
+    // = ceil(CTAs / resident CTAs): pick the split with the least of it, so a
+    // partly filled last wave costs little.
+    const long long cols = (long long)s.grid_x * s.grid_y;
+    const long long slots = (long long)(ctas_per_sm > 0 ? ctas_per_sm : 2) * (num_sms > 0 ? num_sms : 152);
+    long long best = -1, best_gz = 1;
+    const int gz_max = nz / 4 > 1 ? nz / 4 : 1;
+    for (int gz = 1; gz <= gz_max; ++gz) {
+        const long long planes = (nz + gz - 1) / gz;
+        const long long waves = (cols * gz + slots - 1) / slots;
+        const long long cost = waves * (planes + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_gz = gz;
+        }
+    }
+    const int planes = (nz + (int)best_gz - 1) / (int)best_gz;
+    s.rows = planes;
+    s.nblocks = (int)(cols * ((nz + planes - 1) / planes));
     return s;
+}
+
+int d3q19_ctas_per_sm(int precision)
+{
+    int n = 0;
+    cudaError_t e = precision == 0
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &n, d3q19_pass_kernel<double, PASS_STATE>, TX3 * TY3, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &n, d3q19_pass_kernel<float, PASS_STATE>, TX3 * TY3, 0);
+    return e == cudaSuccess && n > 0 ? n : 2;
 }
 
 cudaError_t d3q19_pass(int precision, int pass, const void *params, const PassArgs &a,
@@ -477,6 +473,14 @@ cudaError_t d3q19_pass(int precision, int pass, const void *params, const PassAr
 {
     return precision == 0 ? pass3_t<double>(pass, params, a, s, phi_work, st)
                           : pass3_t<float>(pass, params, a, s, phi_work, st);
+}
+
+cudaError_t d3q19_init_mu_fp64(const void *params, const double *phi0, double *mu, cudaStream_t st)
+{
+    const StepParams<double> &P = *static_cast<const StepParams<double> *>(params);
+    const unsigned nb = (unsigned)((P.N + 255) / 256);
+    d3q19_init_mu<<<nb, 256, 0, st>>>(P, phi0, mu);
+    return cudaGetLastError();
 }
 
 cudaError_t d3q19_init(int precision, const void *params, const double *phi0, double *mu_tmp,

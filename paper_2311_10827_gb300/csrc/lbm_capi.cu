@@ -39,6 +39,10 @@ struct lbm_ctx {
     int nf;      // f arrays: Q, plus the low word of the rest population in FP32
     long long N;
     size_t esz;  // bytes per stored population value
+    int codec;   // offset storage: OFFSET_F16 / OFFSET_BF16, else -1
+    size_t fbytes, gbytes;  // bytes of one f / g state buffer
+    float *scw;  // offset storage: target scales [2], then 2 words of scratch
+    int nsm;
     void *f[2], *g[2], *S;
     int cur;     // f[cur], g[cur] hold the current state
     double *aux;         // N doubles (initial chemical potential)
@@ -110,7 +114,13 @@ int validate(const lbm_grid *g, int lattice, const lbm_params *p)
     if (!finite_pos(p->nu_l) || !finite_pos(p->nu_v)) return LBM_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(p->body_force[a])) return LBM_ERR_INVALID_ARG;
-    if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return LBM_ERR_INVALID_ARG;
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32 &&
+        p->precision != LBM_FP32_F16OFF && p->precision != LBM_FP32_BF16OFF)
+        return LBM_ERR_INVALID_ARG;
+    // 16-bit offset storage is built for the D3Q19 path
+    if ((p->precision == LBM_FP32_F16OFF || p->precision == LBM_FP32_BF16OFF) &&
+        lattice != LBM_D3Q19)
+        return LBM_ERR_INVALID_ARG;
     if (p->diag_every < 0) return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
@@ -166,10 +176,32 @@ int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p
     a.out_u = o_u;
     a.out_mu = o_mu;
     a.partials = ctx->partials;
-    if (ctx->lattice == LBM_D3Q19)
+    if (ctx->codec >= 0)
+        CK(d3q19_off_pass(ctx->codec, pass, &ctx->pf, a, ctx->shape, ctx->phiw, ctx->scw, st));
+    else if (ctx->lattice == LBM_D3Q19)
         CK(d3q19_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, ctx->phiw, st));
     else
         CK(d2q9_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, st));
+    return LBM_OK;
+}
+
+// offset storage: new target scales from the current state
+int refresh_scales(lbm_ctx *ctx, cudaStream_t st)
+{
+    if (ctx->codec < 0) return LBM_OK;
+    CK(offset_refresh(ctx->codec, ctx->N, ctx->Q, ctx->f[ctx->cur], ctx->g[ctx->cur],
+                      (unsigned *)(ctx->scw + 2), ctx->scw, ctx->nsm, st));
+    return LBM_OK;
+}
+
+const float OFFSET_INITIAL_SCALES[2] = {OFFSET_SCALE_FLOOR, OFFSET_SCALE_FLOOR};
+
+// offset storage: targets back to the initial scales (before a new state is written)
+int reset_scales(lbm_ctx *ctx)
+{
+    if (ctx->codec < 0) return LBM_OK;
+    CK(cudaMemcpyAsync(ctx->scw, OFFSET_INITIAL_SCALES, sizeof OFFSET_INITIAL_SCALES,
+                       cudaMemcpyHostToDevice, ctx->stream));
     return LBM_OK;
 }
 
@@ -228,8 +260,8 @@ void fill_diag(const DiagPartial &r, long long step, lbm_diag *out)
 void free_all(lbm_ctx *c)
 {
     if (c->gexec_valid) cudaGraphExecDestroy(c->gexec);
-    void *dev[] = {c->f[0], c->f[1], c->g[0],     c->g[1], c->S,
-                   c->aux,  c->phiw, c->stage,    c->partials, c->dres};
+    void *dev[] = {c->f[0], c->f[1], c->g[0],     c->g[1],     c->S,  c->aux,
+                   c->phiw, c->stage, c->partials, c->dres, c->scw};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hres) cudaFreeHost(c->hres);
@@ -279,6 +311,21 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
     ctx->nf = ctx->Q + (params->precision == LBM_FP32 ? 1 : 0);
     ctx->N = (long long)grid->nx * grid->ny * grid->nz;
     ctx->esz = params->precision == LBM_FP64 ? 8 : 4;
+    ctx->codec = params->precision == LBM_FP32_F16OFF    ? OFFSET_F16
+                 : params->precision == LBM_FP32_BF16OFF ? OFFSET_BF16
+                                                         : -1;
+    if (ctx->codec >= 0) {
+        const OffsetLayout L = offset_layout(ctx->N, ctx->Q, ctx->D);
+        ctx->nf = ctx->Q;
+        ctx->esz = 2;
+        ctx->fbytes = L.fbytes;
+        ctx->gbytes = L.gbytes;
+    } else {
+        ctx->fbytes = (size_t)ctx->nf * ctx->N * ctx->esz;
+        ctx->gbytes = (size_t)ctx->Q * ctx->N * ctx->esz;
+    }
+    // S_prev and the D3Q19 phi work field: FP64 in the FP64 form, else FP32
+    const size_t ssz = params->precision == LBM_FP64 ? 8 : 4;
     ctx->stream = (cudaStream_t)cuda_stream;
 
     // Eqs. beta and suiface_tension solved for kappa and beta; Eq. mobility.
@@ -302,8 +349,14 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
         free(ctx);
         return LBM_ERR_CUDA;
     }
-    ctx->shape = lattice == LBM_D3Q19 ? d3q19_shape(grid->nx, grid->ny, grid->nz, nsm)
-                                      : d2q9_shape(grid->nx, grid->ny, nsm);
+    ctx->nsm = nsm;
+    if (lattice == LBM_D3Q19) {
+        const int occ = ctx->codec >= 0 ? d3q19_off_ctas_per_sm(ctx->codec)
+                                        : d3q19_ctas_per_sm(params->precision);
+        ctx->shape = d3q19_shape(grid->nx, grid->ny, grid->nz, nsm, occ);
+    } else {
+        ctx->shape = d2q9_shape(grid->nx, grid->ny, nsm);
+    }
     ctx->npart = ctx->shape.nblocks;
     const size_t N = (size_t)ctx->N, Q = (size_t)ctx->Q;
     bool oom = false;
@@ -314,13 +367,15 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
             oom = true;
         }
     };
-    dalloc(&ctx->f[0], (size_t)ctx->nf * N * ctx->esz);
-    dalloc(&ctx->f[1], (size_t)ctx->nf * N * ctx->esz);
-    dalloc(&ctx->g[0], Q * N * ctx->esz);
-    dalloc(&ctx->g[1], Q * N * ctx->esz);
-    dalloc(&ctx->S, N * ctx->esz);
+    (void)Q;
+    dalloc(&ctx->f[0], ctx->fbytes);
+    dalloc(&ctx->f[1], ctx->fbytes);
+    dalloc(&ctx->g[0], ctx->gbytes);
+    dalloc(&ctx->g[1], ctx->gbytes);
+    dalloc(&ctx->S, N * ssz);
     dalloc((void **)&ctx->aux, N * sizeof(double));
-    if (lattice == LBM_D3Q19) dalloc(&ctx->phiw, N * ctx->esz);
+    if (lattice == LBM_D3Q19) dalloc(&ctx->phiw, N * ssz);
+    if (ctx->codec >= 0) dalloc((void **)&ctx->scw, 4 * sizeof(float));
     dalloc((void **)&ctx->partials, (size_t)ctx->npart * sizeof(DiagPartial));
     dalloc((void **)&ctx->dres, 2 * sizeof(DiagPartial));
     if (!oom && cudaMallocHost((void **)&ctx->hres, 2 * sizeof(DiagPartial)) != cudaSuccess)
@@ -335,6 +390,13 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
         return LBM_ERR_OOM;
     }
     memset(ctx->hres, 0, 2 * sizeof(DiagPartial));
+    if (ctx->codec >= 0 &&
+        (reset_scales(ctx) != LBM_OK || cudaStreamSynchronize(ctx->stream) != cudaSuccess)) {
+        cudaGetLastError();
+        free_all(ctx);
+        free(ctx);
+        return LBM_ERR_CUDA;
+    }
     *out = ctx;
     return LBM_OK;
 }
@@ -357,11 +419,20 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
         }
         src = tmp;
     }
-    cudaError_t e = ctx->lattice == LBM_D3Q19
-                        ? d3q19_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0],
-                                     ctx->g[0], ctx->S, ctx->stream)
-                        : d2q9_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0],
-                                    ctx->g[0], ctx->S, ctx->stream);
+    cudaError_t e = cudaSuccess;
+    if (ctx->codec >= 0) {
+        e = cudaMemcpyAsync(ctx->scw, OFFSET_INITIAL_SCALES, sizeof OFFSET_INITIAL_SCALES,
+                            cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = d3q19_off_init(ctx->codec, &ctx->pd, &ctx->pf, src, ctx->aux, ctx->f[0],
+                               ctx->g[0], ctx->S, OFFSET_INITIAL_SCALES, ctx->stream);
+    } else if (ctx->lattice == LBM_D3Q19) {
+        e = d3q19_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0], ctx->g[0],
+                       ctx->S, ctx->stream);
+    } else {
+        e = d2q9_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0], ctx->g[0],
+                      ctx->S, ctx->stream);
+    }
     if (tmp) {
         cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
         cudaFree(tmp);
@@ -400,6 +471,7 @@ int lbm_step(lbm_ctx *ctx, int n)
             ctx->cur ^= 1;
             ctx->step += 1;
             left -= 1;
+            if (int rc2 = refresh_scales(ctx, ctx->stream)) return rc2;
             continue;
         }
         // plain steps up to the next diagnostics step
@@ -467,6 +539,7 @@ int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out)
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     int rc = run_pass(ctx, PASS_DIAG, ctx->stream, nullptr, nullptr, nullptr, nullptr);
     if (rc) return rc;
+    if ((rc = refresh_scales(ctx, ctx->stream))) return rc;
     CK(diag_reduce(ctx->partials, ctx->npart, ctx->dres, ctx->stream));
     CK(cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -499,6 +572,9 @@ int lbm_get_state(lbm_ctx *ctx, double *f, double *g, double *S_prev, int on_dev
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     const size_t N = (size_t)ctx->N, QN = (size_t)ctx->Q * N;
     auto get = [&](double *fo, double *go, double *so) {
+        if (ctx->codec >= 0)
+            return d3q19_off_get_state(ctx->codec, &ctx->pf, ctx->f[ctx->cur], ctx->g[ctx->cur],
+                                       ctx->S, fo, go, so, ctx->stream);
         return ctx->lattice == LBM_D3Q19
                    ? d3q19_get_state(ctx->prm.precision, &ctx->pd, ctx->f[ctx->cur],
                                      ctx->g[ctx->cur], ctx->S, fo, go, so, ctx->stream)
@@ -553,11 +629,20 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g, const double *
         gi = tmp + QN;
         si = tmp + 2 * QN;
     }
-    cudaError_t e = ctx->lattice == LBM_D3Q19
-                        ? d3q19_set_state(ctx->prm.precision, &ctx->pd, ctx->f[0], ctx->g[0],
-                                          ctx->S, fi, gi, si, ctx->stream)
-                        : d2q9_set_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny,
-                                         ctx->f[0], ctx->g[0], ctx->S, fi, gi, si, ctx->stream);
+    cudaError_t e = cudaSuccess;
+    if (ctx->codec >= 0) {
+        e = cudaMemcpyAsync(ctx->scw, OFFSET_INITIAL_SCALES, sizeof OFFSET_INITIAL_SCALES,
+                            cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = d3q19_off_set_state(ctx->codec, &ctx->pf, ctx->f[0], ctx->g[0], ctx->S, fi, gi,
+                                    si, OFFSET_INITIAL_SCALES, ctx->stream);
+    } else if (ctx->lattice == LBM_D3Q19) {
+        e = d3q19_set_state(ctx->prm.precision, &ctx->pd, ctx->f[0], ctx->g[0], ctx->S, fi, gi,
+                            si, ctx->stream);
+    } else {
+        e = d2q9_set_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny, ctx->f[0], ctx->g[0],
+                           ctx->S, fi, gi, si, ctx->stream);
+    }
     if (tmp) {
         cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
         cudaFree(tmp);
@@ -572,6 +657,9 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g, const double *
 }
 
 namespace {
+// bytes of one S_prev value
+size_t state_S_bytes(const lbm_ctx *ctx) { return ctx->prm.precision == LBM_FP64 ? 8 : 4; }
+
 struct SaveHeader {
     char magic[8];
     int version, lattice, precision, Q;
@@ -583,9 +671,8 @@ struct SaveHeader {
 int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
 {
     if (!ctx || !bytes) return LBM_ERR_INVALID_ARG;
-    const size_t N = (size_t)ctx->N, popf = (size_t)ctx->nf * N * ctx->esz,
-                 pop = (size_t)ctx->Q * N * ctx->esz;
-    const size_t need = sizeof(SaveHeader) + popf + pop + N * ctx->esz;
+    const size_t N = (size_t)ctx->N, popf = ctx->fbytes, pop = ctx->gbytes, ssz = state_S_bytes(ctx);
+    const size_t need = sizeof(SaveHeader) + popf + pop + N * ssz;
     if (!buf) {
         *bytes = need;
         return LBM_OK;
@@ -610,7 +697,7 @@ int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
     b += sizeof h;
     CK(cudaMemcpyAsync(b, ctx->f[ctx->cur], popf, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(b + popf, ctx->g[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(b + popf + pop, ctx->S, N * ctx->esz, cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(b + popf + pop, ctx->S, N * ssz, cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     *bytes = need;
@@ -620,9 +707,8 @@ int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
 int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
 {
     if (!ctx || !buf) return LBM_ERR_INVALID_ARG;
-    const size_t N = (size_t)ctx->N, popf = (size_t)ctx->nf * N * ctx->esz,
-                 pop = (size_t)ctx->Q * N * ctx->esz;
-    const size_t need = sizeof(SaveHeader) + popf + pop + N * ctx->esz;
+    const size_t N = (size_t)ctx->N, popf = ctx->fbytes, pop = ctx->gbytes, ssz = state_S_bytes(ctx);
+    const size_t need = sizeof(SaveHeader) + popf + pop + N * ssz;
     if (bytes < need) return LBM_ERR_INVALID_ARG;
     SaveHeader h;
     memcpy(&h, buf, sizeof h);
@@ -635,7 +721,7 @@ int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
     const char *b = (const char *)buf + sizeof h;
     CK(cudaMemcpyAsync(ctx->f[0], b, popf, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->g[0], b + popf, pop, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->S, b + popf + pop, N * ctx->esz, cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(ctx->S, b + popf + pop, N * ssz, cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->cur = 0;
@@ -680,7 +766,14 @@ int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value)
     const int *c = ctx->lattice == LBM_D3Q19 ? HC3[i] : HC2[i];
     const int xs = ((x - c[0]) % nx + nx) % nx, ys = ((y - c[1]) % ny + ny) % ny,
               zs = ((z - c[2]) % nz + nz) % nz;
-    const size_t m = (size_t)i * ctx->N + ((size_t)zs * ny + ys) * nx + xs;
+    const size_t node = ((size_t)zs * ny + ys) * nx + xs;
+    if (ctx->codec >= 0) {
+        CK(d3q19_off_poke(ctx->codec, &ctx->pf, ctx->f[ctx->cur], ctx->g[ctx->cur], field, i, node,
+                          value, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return LBM_OK;
+    }
+    const size_t m = (size_t)i * ctx->N + node;
     char *base = (char *)(field == 0 ? ctx->f[ctx->cur] : ctx->g[ctx->cur]);
     if (ctx->esz == 8) {
         CK(cudaMemcpyAsync(base + m * 8, &value, 8, cudaMemcpyHostToDevice, ctx->stream));
@@ -1068,10 +1161,12 @@ struct lbm_adjoint {
     size_t snap;        // bytes of one state snapshot (f, g, S at the context's precision)
     char *ckpt;         // (max_steps / K + 1) snapshots
     char *seg;          // K snapshots of the segment being reversed
+    int real;           // adjoint arithmetic: 0 FP64, 1 FP32 (the context's precision)
+    size_t rsz;         // bytes per adjoint value
     double *phi0;       // N
-    double *lf[2], *lg[2], *lS[2];
+    void *lf[2], *lg[2], *lS[2];  // adjoint fields at the adjoint precision
     double *macro;      // phi, mu, p (N each), u (2N)
-    double *work;       // 7N
+    void *work;         // 7N adjoint values (at least N doubles)
     double *dpar;       // 3
 };
 
@@ -1079,8 +1174,7 @@ namespace {
 
 int snapshot(lbm_ctx *ctx, char *dst, size_t snap)
 {
-    const size_t N = (size_t)ctx->N, fb = (size_t)ctx->nf * N * ctx->esz,
-                 gb = (size_t)ctx->Q * N * ctx->esz;
+    const size_t N = (size_t)ctx->N, fb = ctx->fbytes, gb = ctx->gbytes;
     (void)snap;
     CK(cudaMemcpyAsync(dst, ctx->f[ctx->cur], fb, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(dst + fb, ctx->g[ctx->cur], gb, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1090,8 +1184,7 @@ int snapshot(lbm_ctx *ctx, char *dst, size_t snap)
 
 int restore(lbm_ctx *ctx, const char *src, long long step)
 {
-    const size_t N = (size_t)ctx->N, fb = (size_t)ctx->nf * N * ctx->esz,
-                 gb = (size_t)ctx->Q * N * ctx->esz;
+    const size_t N = (size_t)ctx->N, fb = ctx->fbytes, gb = ctx->gbytes;
     CK(cudaMemcpyAsync(ctx->f[0], src, fb, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->g[0], src + fb, gb, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->S, src + fb + gb, N * ctx->esz, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1130,16 +1223,18 @@ int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_ad
     a->snap = ((size_t)ctx->nf * N + Q * N + N) * ctx->esz;
     a->snap = (a->snap + 255) / 256 * 256;
     const size_t nck = (size_t)(max_steps / checkpoint_every + 1);
+    a->real = ctx->prm.precision == LBM_FP64 ? 0 : 1;
+    a->rsz = a->real == 0 ? sizeof(double) : sizeof(float);
     bool ok = cudaMalloc((void **)&a->ckpt, nck * a->snap) == cudaSuccess &&
               cudaMalloc((void **)&a->seg, (size_t)checkpoint_every * a->snap) == cudaSuccess &&
               cudaMalloc((void **)&a->phi0, N * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&a->macro, 5 * N * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void **)&a->work, 7 * N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&a->work, 7 * N * a->rsz) == cudaSuccess &&
               cudaMalloc((void **)&a->dpar, 3 * sizeof(double)) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b)
-        ok = cudaMalloc((void **)&a->lf[b], Q * N * sizeof(double)) == cudaSuccess &&
-             cudaMalloc((void **)&a->lg[b], Q * N * sizeof(double)) == cudaSuccess &&
-             cudaMalloc((void **)&a->lS[b], N * sizeof(double)) == cudaSuccess;
+        ok = cudaMalloc(&a->lf[b], Q * N * a->rsz) == cudaSuccess &&
+             cudaMalloc(&a->lg[b], Q * N * a->rsz) == cudaSuccess &&
+             cudaMalloc(&a->lS[b], N * a->rsz) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         adjoint_free(a);
@@ -1180,11 +1275,11 @@ int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, d
     const size_t N = (size_t)ctx->N;
     const int nx = ctx->grid.nx, ny = ctx->grid.ny;
     // the seed: dL/dphi of the final state into the adjoint of every f_i
-    double *seed = a->work;
+    double *seed = (double *)a->work;  // 7 N adjoint values hold N doubles
     CK(cudaMemcpyAsync(seed, dL_dphi, N * sizeof(double),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     int cb = 0;
-    CK(adj_d2q9_seed((int)N, seed, a->lf[cb], a->lg[cb], a->lS[cb], ctx->stream));
+    CK(adj_d2q9_seed(a->real, (int)N, seed, a->lf[cb], a->lg[cb], a->lS[cb], ctx->stream));
     CK(cudaMemsetAsync(a->dpar, 0, 3 * sizeof(double), ctx->stream));
     double *phi = a->macro, *mu = a->macro + N, *p = a->macro + 2 * N, *u = a->macro + 3 * N;
     const int nseg = (a->nsteps + a->K - 1) / a->K;
@@ -1202,15 +1297,16 @@ int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, d
         for (int j = len - 1; j >= 0; --j) {
             if (int rc = restore(ctx, a->seg + (size_t)j * a->snap, t0 + j)) return rc;
             if (int rc = run_pass(ctx, PASS_MACROS, ctx->stream, phi, p, u, mu)) return rc;
-            CK(adj_d2q9_step(ctx->prm.precision, &ctx->pd, nx, ny, ctx->f[0], ctx->g[0], ctx->S,
-                             phi, mu, p, u, a->lf[cb], a->lg[cb], a->lS[cb], a->lf[cb ^ 1],
-                             a->lg[cb ^ 1], a->lS[cb ^ 1], a->work, a->dpar, ctx->stream));
+            CK(adj_d2q9_step(a->real, &ctx->pd, nx, ny, ctx->f[0], ctx->g[0], phi, mu, p, u,
+                             a->lf[cb], a->lg[cb], a->lS[cb], a->lf[cb ^ 1], a->lg[cb ^ 1],
+                             a->lS[cb ^ 1], a->work, a->dpar, ctx->stream));
             cb ^= 1;
         }
     }
     // initial condition f = f^eq(phi0, mu(phi0))
     double *lphi0 = on_device ? dL_dphi0 : a->macro;
-    CK(adj_d2q9_init(&ctx->pd, nx, ny, a->phi0, a->lf[cb], a->work, lphi0, a->dpar, ctx->stream));
+    CK(adj_d2q9_init(a->real, &ctx->pd, nx, ny, a->phi0, a->lf[cb], a->work, lphi0, a->dpar,
+                     ctx->stream));
     double dp[3];
     CK(cudaMemcpyAsync(dp, a->dpar, sizeof dp, cudaMemcpyDeviceToHost, ctx->stream));
     if (!on_device)

@@ -82,7 +82,10 @@ cudaError_t d2q9_set_state(int precision, int nx, int ny, void *f, void *g, void
 
 // D3Q19 (kernels_d3q19.cu); a pass first writes phi into phi_work (N values
 // at the context's precision)
-LaunchShape d3q19_shape(int nx, int ny, int nz, int num_sms);
+LaunchShape d3q19_shape(int nx, int ny, int nz, int num_sms, int ctas_per_sm);
+// resident CTAs per SM of the time-step kernel (occupancy query)
+int d3q19_ctas_per_sm(int precision);
+int d3q19_off_ctas_per_sm(int codec);
 cudaError_t d3q19_pass(int precision, int pass, const void *params, const PassArgs &a,
                        const LaunchShape &s, void *phi_work, cudaStream_t st);
 cudaError_t d3q19_init(int precision, const void *params, const double *phi0, double *mu_tmp,
@@ -92,19 +95,61 @@ cudaError_t d3q19_get_state(int precision, const void *params, const void *f, co
 cudaError_t d3q19_set_state(int precision, const void *params, void *f, void *g, void *S,
                             const double *fi, const double *gi, const double *Si, cudaStream_t st);
 
-// D2Q9 discrete adjoint (kernels_adjoint.cu); FP64 adjoint fields in the
-// paper's convention; work holds 7 N doubles; dpar accumulates
-// {dL/dkappa, dL/dbeta, dL/d(1/tau_f)}
-cudaError_t adj_d2q9_seed(int N, const double *dphi, double *lf, double *lg, double *lS,
+// FP64 chemical potential of an initial phi field (Eq. chemical_potencial)
+cudaError_t d3q19_init_mu_fp64(const void *params, const double *phi0, double *mu, cudaStream_t st);
+
+// Populations stored as 16-bit offsets from their equilibria
+// (kernels_d3q19_off.cu).  One parity of the state: the f buffer holds the
+// Q offset arrays (u16), then D + 3 FP32 macro arrays (phi, mu, p, u), then
+// the two FP32 scales (s_f, s_g); the g buffer holds the Q offset arrays.
+enum : int { OFFSET_F16 = 0, OFFSET_BF16 = 1 };
+constexpr float OFFSET_SCALE_FLOOR = 1.0f / 65536.0f;  // 2^-16
+constexpr float OFFSET_HEADROOM = 4096.0f;             // max |stored| after a refresh
+struct OffsetLayout {
+    size_t mac_off, sc_off, fbytes, gbytes;
+};
+__host__ __device__ inline OffsetLayout offset_layout(long long N, int Q, int D)
+{
+    const size_t n = (size_t)N, a = 256;
+    OffsetLayout L;
+    L.mac_off = ((size_t)Q * n * 2 + a - 1) / a * a;
+    L.sc_off = L.mac_off + (((size_t)(D + 3) * n * 4 + a - 1) / a * a);
+    L.fbytes = L.sc_off + a;
+    L.gbytes = (size_t)Q * n * 2;
+    return L;
+}
+cudaError_t d3q19_off_pass(int codec, int pass, const void *params32, const PassArgs &a,
+                           const LaunchShape &s, void *phi_work, const float *target,
+                           cudaStream_t st);
+cudaError_t d3q19_off_init(int codec, const void *params64, const void *params32,
+                           const double *phi0, double *mu_tmp, void *f, void *g, void *S,
+                           const float *target_host, cudaStream_t st);
+cudaError_t d3q19_off_get_state(int codec, const void *params32, const void *f, const void *g,
+                                const void *S, double *fo, double *go, double *So, cudaStream_t st);
+cudaError_t d3q19_off_set_state(int codec, const void *params32, void *f, void *g, void *S,
+                                const double *fi, const double *gi, const double *Si,
+                                const float *target_host, cudaStream_t st);
+cudaError_t d3q19_off_poke(int codec, const void *params32, void *f, void *g, int field, int i,
+                           size_t m, double value, cudaStream_t st);
+// new target scales from the largest stored offsets of the state (f, g);
+// maxbits: 2 device words of scratch; target: the 2 device target scales
+cudaError_t offset_refresh(int codec, long long N, int Q, const void *f, const void *g,
+                           unsigned *maxbits, float *target, int num_sms, cudaStream_t st);
+
+// D2Q9 discrete adjoint (kernels_adjoint.cu) in the paper's convention.
+// Adjoint fields (lf, lg [Q][N], lS [N], work 7 N) are FP64 when real == 0
+// (the FP64 form) and FP32 when real == 1 (the FP32 form); the forward
+// moments (phi, mu, p, u) are FP64; dpar accumulates in FP64
+// {dL/dkappa, dL/dbeta, dL/d(1/tau_f)}.
+cudaError_t adj_d2q9_seed(int real, int N, const double *dphi, void *lf, void *lg, void *lS,
                           cudaStream_t st);
 cudaError_t adj_d2q9_step(int precision, const void *params64, int nx, int ny, const void *f,
-                          const void *g, const void *S, const double *phi, const double *mu,
-                          const double *p, const double *u, const double *lf_in,
-                          const double *lg_in, const double *lS_in, double *lf_out, double *lg_out,
-                          double *lS_out, double *work, double *dpar, cudaStream_t st);
-cudaError_t adj_d2q9_init(const void *params64, int nx, int ny, const double *phi0,
-                          const double *lf, double *work, double *lphi0, double *dpar,
+                          const void *g, const double *phi, const double *mu, const double *p,
+                          const double *u, const void *lf_in, const void *lg_in, const void *lS_in,
+                          void *lf_out, void *lg_out, void *lS_out, void *work, double *dpar,
                           cudaStream_t st);
+cudaError_t adj_d2q9_init(int real, const void *params64, int nx, int ny, const double *phi0,
+                          const void *lf, void *work, double *lphi0, double *dpar, cudaStream_t st);
 
 // diagnostics reduction (kernels_diag.cu): partials[n] -> out (one record)
 cudaError_t diag_reduce(const DiagPartial *partials, int n, DiagPartial *out, cudaStream_t st);

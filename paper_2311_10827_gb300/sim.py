@@ -11,7 +11,8 @@ from . import capi
 
 PARAM_KEYS = ("W", "M", "alpha", "sigma", "phi_l", "phi_v", "rho_l", "rho_v", "nu_l", "nu_v",
               "Gx", "Gy", "Gz", "tau_f")
-PRECISIONS = {"fp64": capi.LBM_FP64, "fp32": capi.LBM_FP32}
+PRECISIONS = {"fp64": capi.LBM_FP64, "fp32": capi.LBM_FP32, "f16off": capi.LBM_FP32_F16OFF,
+              "bf16off": capi.LBM_FP32_BF16OFF}
 LATTICES = {"D2Q9": capi.LBM_D2Q9, "D3Q19": capi.LBM_D3Q19}
 
 

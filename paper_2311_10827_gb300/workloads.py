@@ -105,6 +105,20 @@ DROPLET_PAPER = dict(shape=(128, 128), R=32.0, W=4.0, M=0.1, alpha=1.0, sigma=5e
                      rho_l=10.0, rho_v=1.0, nu_l=0.1, nu_v=0.1)
 
 
+# 3D coalescence: 512^3 periodic, D3Q19, two droplets R = 64 whose centres are
+# 2R + 3 apart (gap 3), W = 5, density ratio 10, other parameters of the
+# 1024^2 droplet.
+COALESCENCE_3D = dict(shape=(512, 512, 512), R=64.0, gap=3.0, W=5.0, M=0.05, alpha=1.0,
+                      sigma=1e-3, rho_l=10.0, rho_v=1.0, nu_l=1.0, nu_v=0.1)
+# Its reduced copy for comparisons with the FP64 oracle: 64^3, R = 8, same W.
+COALESCENCE_3D_SMALL = dict(COALESCENCE_3D, shape=(64, 64, 64), R=8.0)
+# Two-droplet coalescence of Section 3.3 (512^2, M = 0.1, alpha = 1, sigma = 5e-3,
+# W = 8, nu_v = 0.1, centres 2R + W apart) with R = 48, density ratio 10 and
+# equal viscosities: the differentiated run.
+COALESCENCE_ADJ = dict(shape=(512, 512), R=48.0, W=8.0, M=0.1, alpha=1.0, sigma=5e-3,
+                       rho_l=10.0, rho_v=1.0, nu_l=0.1, nu_v=0.1)
+
+
 def physical(params: dict) -> dict:
-    """Strip workload-only keys (shape, R) from a parameter set."""
-    return {k: v for k, v in params.items() if k not in ("shape", "R")}
+    """Strip workload-only keys (shape, R, gap) from a parameter set."""
+    return {k: v for k, v in params.items() if k not in ("shape", "R", "gap")}

@@ -58,6 +58,14 @@ def test_equal_phases_and_bad_grids_rejected(capi):
     assert capi.lbm_create((16, 16), 5, p)[0] == capi.LBM_ERR_INVALID_ARG
 
 
+def test_offset_storage_needs_d3q19(capi):
+    """16-bit offset storage exists for the D3Q19 path only."""
+    for prec in (capi.LBM_FP32_F16OFF, capi.LBM_FP32_BF16OFF):
+        p = capi.lbm_params_default()
+        p.precision = prec
+        assert capi.lbm_create((16, 16), capi.LBM_D2Q9, p)[0] == capi.LBM_ERR_INVALID_ARG
+
+
 def test_null_safety_and_strerror(capi):
     L = capi.lib()
     L.lbm_destroy(None)

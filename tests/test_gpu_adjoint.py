@@ -80,8 +80,8 @@ def test_gpu_adjoint_finite_differences_32x32_50_steps(env):
 
 
 def test_gpu_adjoint_fp32_forward_close_to_fp64(env):
-    """FP32 forward (FP64 reverse step) on the same problem: gradients within
-    the FP32 forward's rounding of the FP64 ones."""
+    """FP32 forward and FP32 reverse step on the same problem: gradients
+    within FP32 rounding (accumulated over the run) of the FP64 ones."""
     shape, n = (64, 48), 60
     phi0 = wl.two_droplets(64, 48, 8.0, 4.0)
     target = np.roll(phi0, 3, axis=1) * 0.95 + 0.02

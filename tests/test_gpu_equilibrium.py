@@ -2,12 +2,16 @@
 128 x 128, R = 0.25 L, W = 4, M = 0.1, alpha = 1, sigma = 5e-3, rho_v = 1,
 nu_v = 0.1, density ratio 10) run to steady state.
 
-* FP64 reaches the magnitudes the paper quotes for its model
-  (tests/golden/paper_magnitudes.json: E O(1e-25), maximum velocity O(1e-16),
-  Section 3.2) and the FP64 path stays in parity with the oracle (checked
-  elsewhere), so this pins the long-run behaviour of the CUDA path;
-* FP32 (compensated rest population) on the same run: spurious |u| at or
-  below 1e-6 and phi within 1e-5 of the FP64 steady state."""
+* FP64 reaches the magnitudes the paper quotes for this case
+  (tests/golden/paper_magnitudes.json, "droplet_rho10": E O(1e-25), spurious
+  velocity O(1e-15)); the FP64 path is in parity with the oracle (checked
+  elsewhere), so this pins the long-run behaviour of the CUDA path.  The
+  slowest mode (the droplet's shape relaxing by diffusion) needs about 6
+  million steps on GB300 (measured: max |u| 1.8e-12 after 4M steps, 4.5e-15
+  after 6M).
+* FP32 (compensated rest population and compensated phi in the chemical
+  potential) over the same run: spurious |u| at or below 1e-6 and phi within
+  1e-5 of the FP64 steady state."""
 import json
 import os
 
@@ -20,7 +24,9 @@ pytestmark = pytest.mark.gpu
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_magnitudes.json")))
 PRM = dict(W=4.0, M=0.1, alpha=1.0, sigma=5e-3, rho_l=10.0, rho_v=1.0, nu_l=0.1, nu_v=0.1)
-STEPS = 2_000_000
+CHUNK, MAX_STEPS = 1_000_000, 9_000_000
+SV_TARGET = 10 * GOLD["droplet_rho10"]["sv_final"]  # an order of magnitude of slack
+E_TARGET = 10 * GOLD["droplet_rho10"]["E_final"]
 
 
 @pytest.fixture(scope="module")
@@ -31,27 +37,37 @@ def runs():
     from paper_2311_10827_gb300 import build, sim
     build.build()
     phi0 = wl.droplet(128, 128, 32.0, 4.0)
-    out = {}
-    for prec in ("fp64", "fp32"):
-        s = sim.Simulation((128, 128), precision=prec, **PRM)
-        s.init_phi(phi0)
-        s.step(STEPS)
-        out[prec] = (s.diagnostics(), s.moments())
-    return out
+    s64 = sim.Simulation((128, 128), precision="fp64", **PRM)
+    s64.init_phi(phi0)
+    steps = 0
+    while steps < MAX_STEPS:
+        s64.step(CHUNK)
+        steps += CHUNK
+        d = s64.diagnostics()
+        if d["u_max"] < SV_TARGET and d["kinetic_energy"] < E_TARGET:
+            break
+    s32 = sim.Simulation((128, 128), precision="fp32", **PRM)
+    s32.init_phi(phi0)
+    s32.step(steps)
+    return steps, {"fp64": (s64.diagnostics(), s64.moments()),
+                   "fp32": (s32.diagnostics(), s32.moments())}
 
 
 def test_fp64_droplet_reaches_paper_magnitudes(runs):
-    ref = GOLD["droplet_rho_ratios"]
-    d, m = runs["fp64"]
-    assert d["u_max"] < 100 * ref["sv_final"]  # O(1e-16) quoted
-    assert d["kinetic_energy"] < 1e3 * ref["E_final"]
-    assert d["mu_max"] - d["mu_min"] < 1e-12
+    steps, r = runs
+    d, m = r["fp64"]
+    assert d["u_max"] < SV_TARGET, (steps, d["u_max"])
+    assert d["kinetic_energy"] < E_TARGET, (steps, d["kinetic_energy"])
+    assert d["mu_max"] - d["mu_min"] < 1e-11
     assert not d["nonfinite"]
+    # the droplet keeps its tanh profile (bulk values within 1e-2 of phi_l, phi_v)
+    assert abs(m["phi"].max() - 1.0) < 1e-2 and abs(m["phi"].min()) < 1e-2
 
 
 def test_fp32_droplet_equilibrium_targets(runs):
-    d64, m64 = runs["fp64"]
-    d32, m32 = runs["fp32"]
+    steps, r = runs
+    d64, m64 = r["fp64"]
+    d32, m32 = r["fp32"]
     assert d32["u_max"] <= 1e-6
-    assert np.abs(m32["phi"] - m64["phi"]).max() <= 1e-5
+    assert np.abs(m32["phi"] - m64["phi"]).max() <= 1e-5, steps
     assert np.abs(m32["u"] - m64["u"]).max() <= 1e-6
