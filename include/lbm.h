@@ -67,7 +67,13 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 /* Precision of storage and arithmetic.  LBM_FP64: FP64 throughout (parity
  * form).  LBM_FP32: FP32 populations and arithmetic, the rest population of
  * f kept as a compensated pair of FP32 words (its per-step change near
- * equilibrium is below half an FP32 ulp of phi); diagnostics in FP64.
+ * equilibrium is below half an FP32 ulp of phi), and the f populations
+ * stored minus a uniform equilibrium shift w_i alpha mu_ref (the rest one
+ * plus (1 - w_0) alpha mu_ref): a uniform shift of mu in Eq. H_i changes no
+ * moment the step uses, so it is exact, and with mu_ref near the equilibrium
+ * chemical potential the small per-step changes of the moving populations
+ * are not lost to FP32 rounding; lbm_diagnostics re-centres mu_ref to the
+ * middle of the current mu range.  Diagnostics in FP64.
  * LBM_FP32_F16OFF / LBM_FP32_BF16OFF (D3Q19 only): FP32 arithmetic with every
  * population stored as a 16-bit (FP16 / BF16) offset from its equilibrium
  * (Eq. H_i for f, the g^eq of Eq. G_i for g), evaluated at FP32 macroscopic
@@ -165,9 +171,12 @@ int lbm_step(lbm_ctx *ctx, int n);
 int lbm_moments(lbm_ctx *ctx, double *phi, double *p, double *u, double *mu,
                 int on_device);
 
-/* Diagnostics of the current state (synchronises).  Errors: STATE, CUDA,
- * INVALID_ARG.  A non-finite field is reported through out->nonfinite (the
- * call itself still returns LBM_OK). */
+/* Diagnostics of the current state (synchronises).  For LBM_FP32 it also
+ * re-centres the equilibrium shift of the storage (applied by the next step;
+ * not while an adjoint recorder is attached), and for the offset precisions
+ * it refreshes the scales.  Errors: STATE, CUDA, INVALID_ARG.  A non-finite
+ * field is reported through out->nonfinite (the call itself still returns
+ * LBM_OK). */
 int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
 
 /* Diagnostics recorded by the most recent fused diagnostics step of
@@ -190,7 +199,8 @@ int lbm_last_diagnostics(lbm_ctx *ctx, lbm_diag *out);
  *     params->precision (the layout of the population payload written by
  *     lbm_save: the paper's f_i(x,t) stored at node x - c_i): g is [Q][N];
  *     f is [Q][N] in FP64 and [Q+1][N] in FP32 (the last array holds the
- *     low word of the rest population); S_prev: device array [N]
+ *     low word of the rest population; FP32 f may carry any uniform
+ *     equilibrium shift, which the diagnostics do not see); S_prev: device array [N]
  *     (u.grad(phi) of the previous step).  Read only.
  *   out: device array of 8 doubles, written asynchronously:
  *     {sum phi, E, max |u|^2, mu_min, mu_max, budget, nonfinite (1 or 0), 0}.
@@ -217,7 +227,8 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g,
                   const double *S_prev, long long step, int on_device);
 
 /* Checkpoint to / restore from a host buffer in the library's own format
- * (header, then the raw device state at the context's precision: f, g, S_prev
+ * (header, which also records the FP32 equilibrium shift, then the raw
+ * device state at the context's precision: f, g, S_prev
  * in the storage layout described at lbm_diagnostics_noalloc; for the offset
  * precisions f is the Q offset arrays (u16), the D + 3 FP32 macro arrays
  * (phi, mu, p, u), each padded to 256 bytes, and the two FP32 scales padded

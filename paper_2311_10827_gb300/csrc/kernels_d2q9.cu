@@ -205,6 +205,15 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     // mu halo column handled by threads 0, 1: ring index 0 and TX+1
     const int jM = tx == 0 ? 0 : TX + 1;
 
+    // FP32: equilibrium shift of the source buffer and of the writes (a uniform
+    // shift of mu in f^eq; phi, the moments and the stencils do not see it)
+    T a_src = T(0), a_dst = T(0);
+    if (REST_PAIR) {
+        a_src = *a.eqs_src;
+        a_dst = *a.eqs_target;
+        if ((PASS & PASS_STATE) && x0 == 0 && y0 == 0 && lin == 0) *a.eqs_dst = a_dst;
+    }
+
     // m(row) = dir (row - first) is the march coordinate, >= -2 for every row used
     const int first = dir > 0 ? y0 : yend - 1;
     const int nout = yend - y0;
@@ -420,12 +429,16 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
                 // form f (1 - 1/tau) + f^eq/tau would add (1 - 1/tau + 1/tau - 1)
                 // sum_{i!=0} f_i, a systematic FP32 drift of the phi mass).
                 const T Sh = T(1.5) * S - T(0.5) * Sprev;
-                const T am = P.alpha * mu;
+                // alpha mu in the source buffer's shifted variables; dsh moves
+                // the written values to the target shift (0 unless it changed)
+                const T am = P.alpha * mu - a_src;
+                const T dsh = a_src - a_dst;
                 const T itf = P.inv_tauf;
                 {
                     // f_0* = f_0 - (f_0 - f_0^eq)/tau_f - (8/9) Sh with
                     // f_0 - f_0^eq = (5/9) alpha mu - sum_{i!=0} f_i
-                    const T d0 = -(T(5.0 / 9.0) * am - snz) * itf - T(8.0 / 9.0) * Sh;
+                    const T d0 = -(T(5.0 / 9.0) * am - snz) * itf - T(8.0 / 9.0) * Sh -
+                                 T(5.0 / 9.0) * dsh;
                     if (REST_PAIR) {
                         // (hi, lo) + d0 with an exact two-sum on the high word
                         const T sl = locur + d0;
@@ -439,7 +452,8 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
                     }
                 }
                 const T ea = T(1.0 / 9.0) * am, ed = T(1.0 / 36.0) * am;
-                const T sa = T(-1.0 / 18.0) * Sh, sd = T(1.0 / 36.0) * Sh;
+                const T sa = T(-1.0 / 18.0) * Sh + T(1.0 / 9.0) * dsh;
+                const T sd = T(1.0 / 36.0) * Sh + T(1.0 / 36.0) * dsh;
 #pragma unroll
                 for (int i = 1; i <= 4; ++i)
                     st_stream(fd + (i * N + n), fcur[i] + ((ea - fcur[i]) * itf + sa));
@@ -550,6 +564,9 @@ __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS, TX>::ctas))
     a.S_out = c.S_out;
     a.out_phi = a.out_p = a.out_u = a.out_mu = nullptr;
     a.partials = partials;
+    a.eqs_src = c.eqs + parity;
+    a.eqs_dst = c.eqs + (parity ^ 1);
+    a.eqs_target = c.eqs + 2;
     d2q9_tile<T, TX, PASS>(P, a, t.x0, t.y0, t.yend, t.dir, blockIdx.x);
 }
 
@@ -601,16 +618,20 @@ __global__ void d2q9_init_pop(const StepParams<double> P, const double *__restri
 // paper convention <-> pull storage
 template <typename T>
 __global__ void d2q9_get_state_k(int nx, int ny, const T *__restrict__ f, const T *__restrict__ g,
-                                 const T *__restrict__ S, double *fo, double *go, double *So)
+                                 const T *__restrict__ S, const float *eqs, double *fo,
+                                 double *go, double *So)
 {
     const size_t N = (size_t)nx * ny;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int x = (int)(n % nx), y = (int)(n / nx);
+    const double a = sizeof(T) == 4 ? (double)*eqs : 0.0;  // equilibrium shift
     for (int i = 0; i < 9; ++i) {
         const size_t m = (size_t)wrapi(y - cyv(i), ny) * nx + wrapi(x - cxv(i), nx);
         double fv = (double)f[i * N + m];
         if (sizeof(T) == 4 && i == 0) fv += (double)f[9 * N + m];  // rest population pair
+        if (sizeof(T) == 4)
+            fv += i == 0 ? -(5.0 / 9.0) * a : (i <= 4 ? (1.0 / 9.0) * a : (1.0 / 36.0) * a);
         if (fo) fo[i * N + n] = fv;
         if (go) go[i * N + n] = (double)g[i * N + m];
     }
@@ -727,17 +748,18 @@ cudaError_t d2q9_init(int precision, const void *params, const double *phi0, dou
 }
 
 cudaError_t d2q9_get_state(int precision, int nx, int ny, const void *f, const void *g,
-                           const void *S, double *fo, double *go, double *So, cudaStream_t st)
+                           const void *S, const float *eqs, double *fo, double *go, double *So,
+                           cudaStream_t st)
 {
     const size_t N = (size_t)nx * ny;
     const int tb = 256;
     const unsigned nb = (unsigned)((N + tb - 1) / tb);
     if (precision == 0)
         d2q9_get_state_k<double><<<nb, tb, 0, st>>>(nx, ny, (const double *)f, (const double *)g,
-                                                    (const double *)S, fo, go, So);
+                                                    (const double *)S, eqs, fo, go, So);
     else
         d2q9_get_state_k<float><<<nb, tb, 0, st>>>(nx, ny, (const float *)f, (const float *)g,
-                                                   (const float *)S, fo, go, So);
+                                                   (const float *)S, eqs, fo, go, So);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,15 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
     double d_phi = 0.0, d_E = 0.0, d_u2 = 0.0, d_mumin = DBL_MAX, d_mumax = -DBL_MAX,
            d_bud = 0.0, d_bad = 0.0;
 
+    // FP32: equilibrium shift of the source buffer and of the writes
+    T a_src = T(0), a_dst = T(0);
+    if (sizeof(T) == 4) {
+        a_src = *a.eqs_src;
+        a_dst = *a.eqs_target;
+        if ((PASS & PASS_STATE) && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
+            *a.eqs_dst = a_dst;
+    }
+
     for (int q = 0; q < 5; ++q) load_phi_plane(z0 - 2 + q);
     __syncthreads();
     mu_plane(z0 - 1);
@@ -221,10 +230,11 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
             __stcs(static_cast<T *>(a.S) + n, S);
             // CH population: b = -5/2, -1, 1/2 (rest, face, edge) for D = 3
             const T Sh = T(1.5) * S - T(0.5) * Sprev;
-            const T am = P.alpha * mu;
+            const T am = P.alpha * mu - a_src;  // in the source buffer's shifted variables
+            const T dsh = a_src - a_dst;         // move the writes to the target shift
             const T itf = P.inv_tauf;
             {
-                const T d0 = -(T(2.0 / 3.0) * am - snz) * itf - T(5.0 / 6.0) * Sh;
+                const T d0 = -(T(2.0 / 3.0) * am - snz) * itf - T(5.0 / 6.0) * Sh - T(2.0 / 3.0) * dsh;
                 if (sizeof(T) == 4) {
                     const T sl = lo0 + d0;  // exact two-sum on the high word
                     const T hi = fv[0] + sl;
@@ -238,7 +248,8 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
             // each population moves by its own small increment (as in 2D: the
             // increments sum to sum_i F_i up to unbiased rounding)
             const T ea = T(1.0 / 18.0) * am, ee = T(1.0 / 36.0) * am;
-            const T sa = T(-1.0 / 18.0) * Sh, se = T(1.0 / 72.0) * Sh;
+            const T sa = T(-1.0 / 18.0) * Sh + T(1.0 / 18.0) * dsh;
+            const T se = T(1.0 / 72.0) * Sh + T(1.0 / 36.0) * dsh;
 #pragma unroll
             for (int i = 1; i < 19; ++i)
                 __stcs(fd + (i * N + n), fv[i] + (((i <= 6 ? ea : ee) - fv[i]) * itf + (i <= 6 ? sa : se)));
@@ -360,8 +371,8 @@ __global__ void d3q19_init_pop(const StepParams<double> P, const double *__restr
 
 template <typename T>
 __global__ void d3q19_get_state_k(StepParams<double> P, const T *__restrict__ f,
-                                  const T *__restrict__ g, const T *__restrict__ S, double *fo,
-                                  double *go, double *So)
+                                  const T *__restrict__ g, const T *__restrict__ S,
+                                  const float *eqs, double *fo, double *go, double *So)
 {
     const size_t N = (size_t)P.N;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,6 +384,7 @@ __global__ void d3q19_get_state_k(StepParams<double> P, const T *__restrict__ f,
         const unsigned m = b.at(-c3x(i), -c3y(i), -c3z(i));
         double fv = (double)f[i * N + m];
         if (sizeof(T) == 4 && i == 0) fv += (double)f[19 * N + m];
+        if (sizeof(T) == 4) fv += (i == 0 ? -(2.0 / 3.0) : w3(i)) * (double)*eqs;  // equilibrium shift
         if (fo) fo[i * N + n] = fv;
         if (go) go[i * N + n] = (double)g[i * N + m];
     }
@@ -497,16 +509,17 @@ cudaError_t d3q19_init(int precision, const void *params, const double *phi0, do
 }
 
 cudaError_t d3q19_get_state(int precision, const void *params, const void *f, const void *g,
-                            const void *S, double *fo, double *go, double *So, cudaStream_t st)
+                            const void *S, const float *eqs, double *fo, double *go, double *So,
+                            cudaStream_t st)
 {
     const StepParams<double> &P = *static_cast<const StepParams<double> *>(params);
     const unsigned nb = (unsigned)((P.N + 255) / 256);
     if (precision == 0)
         d3q19_get_state_k<double><<<nb, 256, 0, st>>>(P, (const double *)f, (const double *)g,
-                                                     (const double *)S, fo, go, So);
+                                                     (const double *)S, eqs, fo, go, So);
     else
         d3q19_get_state_k<float><<<nb, 256, 0, st>>>(P, (const float *)f, (const float *)g,
-                                                    (const float *)S, fo, go, So);
+                                                    (const float *)S, eqs, fo, go, So);
     return cudaGetLastError();
 }
 

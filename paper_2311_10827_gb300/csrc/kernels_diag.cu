@@ -2,6 +2,7 @@
 // pass over the grid are combined by one CTA in a fixed order (deterministic:
 // the same partials always give bit-identical results).
 #include <float.h>
+#include <math.h>
 
 #include "lbm_internal.h"
 
@@ -60,11 +61,27 @@ __global__ void __launch_bounds__(RT) diag_reduce_kernel(const DiagPartial *__re
     }
 }
 
+// equilibrium shift target: alpha times the middle of the mu range (at
+// equilibrium mu is uniform, so the stored moving populations become the
+// small non-equilibrium parts)
+__global__ void eq_recentre_kernel(const DiagPartial *rec, double alpha, float *target)
+{
+    const DiagPartial r = *rec;
+    const double a = alpha * 0.5 * (r.mu_min + r.mu_max);
+    if (r.nonfinite == 0.0 && isfinite(a)) *target = (float)a;
+}
+
 }  // namespace
 
 cudaError_t diag_reduce(const DiagPartial *partials, int n, DiagPartial *out, cudaStream_t st)
 {
     diag_reduce_kernel<<<1, RT, 0, st>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t eq_recentre(const DiagPartial *rec, double alpha, float *target, cudaStream_t st)
+{
+    eq_recentre_kernel<<<1, 1, 0, st>>>(rec, alpha, target);
     return cudaGetLastError();
 }
 

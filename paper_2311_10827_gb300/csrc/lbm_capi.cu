@@ -42,6 +42,8 @@ struct lbm_ctx {
     int codec;   // offset storage: OFFSET_F16 / OFFSET_BF16, else -1
     size_t fbytes, gbytes;  // bytes of one f / g state buffer
     float *scw;  // offset storage: target scales [2], then 2 words of scratch
+    float *eqs;  // FP32 equilibrium shift {buffer 0, buffer 1, target} (device)
+    int recentre;  // lbm_diagnostics moves the FP32 equilibrium shift (not under an adjoint)
     int nsm;
     void *f[2], *g[2], *S;
     int cur;     // f[cur], g[cur] hold the current state
@@ -176,6 +178,9 @@ int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p
     a.out_u = o_u;
     a.out_mu = o_mu;
     a.partials = ctx->partials;
+    a.eqs_src = ctx->eqs + ctx->cur;
+    a.eqs_dst = ctx->eqs + (ctx->cur ^ 1);
+    a.eqs_target = ctx->eqs + 2;
     if (ctx->codec >= 0)
         CK(d3q19_off_pass(ctx->codec, pass, &ctx->pf, a, ctx->shape, ctx->phiw, ctx->scw, st));
     else if (ctx->lattice == LBM_D3Q19)
@@ -195,6 +200,20 @@ int refresh_scales(lbm_ctx *ctx, cudaStream_t st)
 }
 
 const float OFFSET_INITIAL_SCALES[2] = {OFFSET_SCALE_FLOOR, OFFSET_SCALE_FLOOR};
+
+// a new state (initial condition, set_state, load): equilibrium shift `a`
+// for the state in buffer 0 and for new writes
+int set_eq_shift(lbm_ctx *ctx, float a)
+{
+    if (a == 0.0f) {
+        CK(cudaMemsetAsync(ctx->eqs, 0, 3 * sizeof(float), ctx->stream));
+        return LBM_OK;
+    }
+    float v[3] = {a, a, a};
+    CK(cudaMemcpyAsync(ctx->eqs, v, sizeof v, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // v is on the stack
+    return LBM_OK;
+}
 
 // offset storage: targets back to the initial scales (before a new state is written)
 int reset_scales(lbm_ctx *ctx)
@@ -260,8 +279,8 @@ void fill_diag(const DiagPartial &r, long long step, lbm_diag *out)
 void free_all(lbm_ctx *c)
 {
     if (c->gexec_valid) cudaGraphExecDestroy(c->gexec);
-    void *dev[] = {c->f[0], c->f[1], c->g[0],     c->g[1],     c->S,  c->aux,
-                   c->phiw, c->stage, c->partials, c->dres, c->scw};
+    void *dev[] = {c->f[0], c->f[1], c->g[0],     c->g[1], c->S,   c->aux,
+                   c->phiw, c->stage, c->partials, c->dres, c->scw, c->eqs};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hres) cudaFreeHost(c->hres);
@@ -376,6 +395,8 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
     dalloc((void **)&ctx->aux, N * sizeof(double));
     if (lattice == LBM_D3Q19) dalloc(&ctx->phiw, N * ssz);
     if (ctx->codec >= 0) dalloc((void **)&ctx->scw, 4 * sizeof(float));
+    dalloc((void **)&ctx->eqs, 3 * sizeof(float));
+    ctx->recentre = 1;
     dalloc((void **)&ctx->partials, (size_t)ctx->npart * sizeof(DiagPartial));
     dalloc((void **)&ctx->dres, 2 * sizeof(DiagPartial));
     if (!oom && cudaMallocHost((void **)&ctx->hres, 2 * sizeof(DiagPartial)) != cudaSuccess)
@@ -390,8 +411,8 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
         return LBM_ERR_OOM;
     }
     memset(ctx->hres, 0, 2 * sizeof(DiagPartial));
-    if (ctx->codec >= 0 &&
-        (reset_scales(ctx) != LBM_OK || cudaStreamSynchronize(ctx->stream) != cudaSuccess)) {
+    if ((ctx->codec >= 0 && reset_scales(ctx) != LBM_OK) || set_eq_shift(ctx, 0.0f) != LBM_OK ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         free_all(ctx);
         free(ctx);
@@ -420,6 +441,13 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
         src = tmp;
     }
     cudaError_t e = cudaSuccess;
+    if (int rc = set_eq_shift(ctx, 0.0f)) {
+        if (tmp) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(tmp);
+        }
+        return rc;
+    }
     if (ctx->codec >= 0) {
         e = cudaMemcpyAsync(ctx->scw, OFFSET_INITIAL_SCALES, sizeof OFFSET_INITIAL_SCALES,
                             cudaMemcpyHostToDevice, ctx->stream);
@@ -541,6 +569,8 @@ int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out)
     if (rc) return rc;
     if ((rc = refresh_scales(ctx, ctx->stream))) return rc;
     CK(diag_reduce(ctx->partials, ctx->npart, ctx->dres, ctx->stream));
+    if (ctx->prm.precision == LBM_FP32 && ctx->recentre)
+        CK(eq_recentre(ctx->dres, ctx->alpha, ctx->eqs + 2, ctx->stream));
     CK(cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -577,10 +607,11 @@ int lbm_get_state(lbm_ctx *ctx, double *f, double *g, double *S_prev, int on_dev
                                        ctx->S, fo, go, so, ctx->stream);
         return ctx->lattice == LBM_D3Q19
                    ? d3q19_get_state(ctx->prm.precision, &ctx->pd, ctx->f[ctx->cur],
-                                     ctx->g[ctx->cur], ctx->S, fo, go, so, ctx->stream)
+                                     ctx->g[ctx->cur], ctx->S, ctx->eqs + ctx->cur, fo, go, so,
+                                     ctx->stream)
                    : d2q9_get_state(ctx->prm.precision, ctx->grid.nx, ctx->grid.ny,
-                                    ctx->f[ctx->cur], ctx->g[ctx->cur], ctx->S, fo, go, so,
-                                    ctx->stream);
+                                    ctx->f[ctx->cur], ctx->g[ctx->cur], ctx->S,
+                                    ctx->eqs + ctx->cur, fo, go, so, ctx->stream);
     };
     if (on_device) {
         CK(get(f, g, S_prev));
@@ -630,6 +661,13 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g, const double *
         si = tmp + 2 * QN;
     }
     cudaError_t e = cudaSuccess;
+    if (int rc = set_eq_shift(ctx, 0.0f)) {
+        if (tmp) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(tmp);
+        }
+        return rc;
+    }
     if (ctx->codec >= 0) {
         e = cudaMemcpyAsync(ctx->scw, OFFSET_INITIAL_SCALES, sizeof OFFSET_INITIAL_SCALES,
                             cudaMemcpyHostToDevice, ctx->stream);
@@ -663,7 +701,8 @@ size_t state_S_bytes(const lbm_ctx *ctx) { return ctx->prm.precision == LBM_FP64
 struct SaveHeader {
     char magic[8];
     int version, lattice, precision, Q;
-    int nx, ny, nz, pad;
+    int nx, ny, nz;
+    float eq_shift;  // FP32: equilibrium shift of the saved populations
     long long step;
 };
 }  // namespace
@@ -684,7 +723,10 @@ int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes)
     SaveHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, "WBLBMCK", 8);
-    h.version = 1;
+    h.version = 2;
+    CK(cudaMemcpyAsync(&h.eq_shift, ctx->eqs + ctx->cur, sizeof(float), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     h.lattice = ctx->lattice;
     h.precision = ctx->prm.precision;
     h.Q = ctx->Q;
@@ -712,7 +754,7 @@ int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
     if (bytes < need) return LBM_ERR_INVALID_ARG;
     SaveHeader h;
     memcpy(&h, buf, sizeof h);
-    if (memcmp(h.magic, "WBLBMCK", 8) != 0 || h.version != 1 || h.lattice != ctx->lattice ||
+    if (memcmp(h.magic, "WBLBMCK", 8) != 0 || h.version != 2 || h.lattice != ctx->lattice ||
         h.precision != ctx->prm.precision || h.Q != ctx->Q || h.nx != ctx->grid.nx ||
         h.ny != ctx->grid.ny || h.nz != ctx->grid.nz || h.step < 0)
         return LBM_ERR_INVALID_ARG;
@@ -723,6 +765,7 @@ int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes)
     CK(cudaMemcpyAsync(ctx->g[0], b + popf, pop, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->S, b + popf + pop, N * ssz, cudaMemcpyHostToDevice,
                        ctx->stream));
+    if (int rc = set_eq_shift(ctx, h.eq_shift)) return rc;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->cur = 0;
     ctx->step = h.step;
@@ -779,7 +822,18 @@ int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value)
         CK(cudaMemcpyAsync(base + m * 8, &value, 8, cudaMemcpyHostToDevice, ctx->stream));
     } else {
         static const float zero = 0.0f;
-        float v = (float)value;
+        double shifted = value;
+        if (field == 0) {  // stored f is shifted by the equilibrium shift of its buffer
+            float a = 0.0f;
+            CK(cudaMemcpyAsync(&a, ctx->eqs + ctx->cur, sizeof a, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            const double w0 = ctx->lattice == LBM_D3Q19 ? 1.0 / 3.0 : 4.0 / 9.0;
+            const double wi = ctx->lattice == LBM_D3Q19 ? (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0)
+                                                        : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+            shifted -= (i == 0 ? -(1.0 - w0) : wi) * (double)a;
+        }
+        float v = (float)shifted;
         CK(cudaMemcpyAsync(base + m * 4, &v, 4, cudaMemcpyHostToDevice, ctx->stream));
         if (field == 0 && i == 0)  // low word of the rest population pair
             CK(cudaMemcpyAsync(base + (m + (size_t)ctx->Q * ctx->N) * 4, &zero, 4,
@@ -1047,6 +1101,7 @@ int lbm_batch_create(int ncases, const lbm_grid *grids, const lbm_params *params
         h[c].g[1] = x->g[1];
         h[c].S = x->S;
         h[c].S_out = x->S;
+        h[c].eqs = x->eqs;
     }
     const size_t bytes = (size_t)ncases * sizeof(BatchCase);
     bool ok = cudaMalloc((void **)&b->d_cases, bytes) == cudaSuccess &&
@@ -1240,6 +1295,7 @@ int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_ad
         adjoint_free(a);
         return LBM_ERR_OOM;
     }
+    ctx->recentre = 0;  // the recorded states keep one equilibrium shift
     *out = a;
     return LBM_OK;
 }
@@ -1333,6 +1389,7 @@ void lbm_adjoint_destroy(lbm_adjoint *a)
     if (!a) return;
     cudaSetDevice(a->ctx->device);
     cudaStreamSynchronize(a->ctx->stream);
+    a->ctx->recentre = 1;
     adjoint_free(a);
 }
 

@@ -43,7 +43,21 @@ struct PassArgs {
     void *S_out;          // S out (same node; may equal S: in place)
     double *out_phi, *out_p, *out_u, *out_mu;
     DiagPartial *partials;
+    // FP32 equilibrium shift a (see below): of the source buffer, of the
+    // destination buffer (written by the step) and the target for new writes
+    const float *eqs_src;
+    float *eqs_dst;
+    const float *eqs_target;
 };
+
+// FP32 storage holds the f populations shifted by a uniform equilibrium
+// a = alpha mu_ref: f~_i = f_i - w_i a (i != 0), f~_0 = f_0 + (1 - w_0) a.  A
+// uniform shift of mu in f^eq is an exact symmetry of the discrete step (it
+// streams unchanged, relaxes unchanged, and leaves phi = sum_i f_i and every
+// other moment the step uses unchanged), so it is free to choose; with mu_ref
+// near the equilibrium chemical potential the stored moving populations are
+// small and their per-step changes are not lost to FP32 rounding.  Each
+// context keeps {a of buffer 0, a of buffer 1, target} on the device.
 
 struct LaunchShape {
     int rows;      // rows per CTA (2D march length)
@@ -59,6 +73,7 @@ struct BatchCase {
     StepParams<float> pf;
     void *f[2], *g[2];
     void *S, *S_out;
+    float *eqs;  // the grid's equilibrium shifts {buffer 0, buffer 1, target}
 };
 // One CTA's tile of a batch: case, strip x0, rows [y0, yend), march direction.
 struct BatchTile {
@@ -75,7 +90,8 @@ cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
 cudaError_t d2q9_init(int precision, const void *params, const double *phi0, double *mu_tmp,
                       void *f, void *g, void *S, cudaStream_t st);
 cudaError_t d2q9_get_state(int precision, int nx, int ny, const void *f, const void *g,
-                           const void *S, double *fo, double *go, double *So, cudaStream_t st);
+                           const void *S, const float *eqs, double *fo, double *go, double *So,
+                           cudaStream_t st);
 cudaError_t d2q9_set_state(int precision, int nx, int ny, void *f, void *g, void *S,
                            const double *fi, const double *gi, const double *Si,
                            cudaStream_t st);
@@ -91,7 +107,8 @@ cudaError_t d3q19_pass(int precision, int pass, const void *params, const PassAr
 cudaError_t d3q19_init(int precision, const void *params, const double *phi0, double *mu_tmp,
                        void *f, void *g, void *S, cudaStream_t st);
 cudaError_t d3q19_get_state(int precision, const void *params, const void *f, const void *g,
-                            const void *S, double *fo, double *go, double *So, cudaStream_t st);
+                            const void *S, const float *eqs, double *fo, double *go, double *So,
+                            cudaStream_t st);
 cudaError_t d3q19_set_state(int precision, const void *params, void *f, void *g, void *S,
                             const double *fi, const double *gi, const double *Si, cudaStream_t st);
 
@@ -153,5 +170,8 @@ cudaError_t adj_d2q9_init(int real, const void *params64, int nx, int ny, const 
 
 // diagnostics reduction (kernels_diag.cu): partials[n] -> out (one record)
 cudaError_t diag_reduce(const DiagPartial *partials, int n, DiagPartial *out, cudaStream_t st);
+// new equilibrium-shift target alpha (mu_min + mu_max) / 2 from a reduced
+// diagnostics record (kept if the record is not finite)
+cudaError_t eq_recentre(const DiagPartial *rec, double alpha, float *target, cudaStream_t st);
 
 }  // namespace wblbm
