@@ -36,6 +36,10 @@ __device__ __forceinline__ int wrapi(int c, int n)
     int r = c % n;
     return r < 0 ? r + n : r;
 }
+// wrap of c in [-n, 2n) without a division
+__device__ __forceinline__ int wrap1(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+// wrap of any c; `small` (a uniform flag) when c may leave [-n, 2n)
+__device__ __forceinline__ int wrapc(int c, int n, bool small) { return small ? wrapi(c, n) : wrap1(c, n); }
 
 template <typename T>
 struct Arith3;
@@ -55,14 +59,19 @@ struct Nb {
     __device__ unsigned at(int dx, int dy, int dz) const { return zs[dz + 1] + ys[dy + 1] + xs[dx + 1]; }
 };
 
+// x, y, z in [0, n): the neighbours at -1..1 wrap without a division
+__device__ __forceinline__ void nb_plane(Nb &b, int z, int nx, int ny, int nz)
+{
+    for (int d = -1; d <= 1; ++d) b.zs[d + 1] = (unsigned)wrap1(z + d, nz) * (unsigned)(nx * ny);
+}
 __device__ __forceinline__ Nb make_nb(int x, int y, int z, int nx, int ny, int nz)
 {
     Nb b;
     for (int d = -1; d <= 1; ++d) {
-        b.xs[d + 1] = (unsigned)wrapi(x + d, nx);
-        b.ys[d + 1] = (unsigned)wrapi(y + d, ny) * nx;
-        b.zs[d + 1] = (unsigned)wrapi(z + d, nz) * nx * ny;
+        b.xs[d + 1] = (unsigned)wrap1(x + d, nx);
+        b.ys[d + 1] = (unsigned)wrap1(y + d, ny) * nx;
     }
+    nb_plane(b, z, nx, ny, nz);
     return b;
 }
 

@@ -25,15 +25,18 @@ namespace {
 using namespace d3;
 
 // phi = sum_i f_i(x - c_i): rest population last, moving ones in fixed pairs
+// grid (ceil(nx / PHI_TX), ny, nz): one thread per node of a row
+constexpr int PHI_TX = 128;
 template <typename T>
-__global__ void d3q19_phi_kernel(const StepParams<T> P, const T *__restrict__ f, T *__restrict__ phi)
+__global__ void __launch_bounds__(PHI_TX)
+    d3q19_phi_kernel(const StepParams<T> P, const T *__restrict__ f, T *__restrict__ phi)
 {
-    const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned N = (unsigned)P.N;
-    if (n >= N) return;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    const int x = blockIdx.x * PHI_TX + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const unsigned N = (unsigned)P.N;
     const Nb b = make_nb(x, y, z, nx, ny, nz);
+    const unsigned n = b.at(0, 0, 0);
     T v[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) v[i] = __ldg(f + (i * N + b.at(-c3x(i), -c3y(i), -c3z(i))));
@@ -67,12 +70,14 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
     auto pslot = [&](int zz) { return (zz - z0 + 2) % RP; };  // zz >= z0 - 2
     auto mslot = [&](int zz) { return (zz - z0 + 1) % RM; };  // zz >= z0 - 1
 
+    // grids narrower than a tile plus halo wrap by division (uniform flags)
+    const bool smx = nx < PX + 2, smy = ny < PY + 2, smz = nz < 8;
     auto load_phi_plane = [&](int zz) {
         T *dst = phs + pslot(zz) * PA;
-        const unsigned zo = (unsigned)wrapi(zz, nz) * plane;
+        const unsigned zo = (unsigned)wrapc(zz, nz, smz) * plane;
         for (int q = tid; q < PA; q += TX3 * TY3) {
             const int lx = q % PX, ly = q / PX;
-            const unsigned xx = wrapi(x0 - 2 + lx, nx), yy = wrapi(y0 - 2 + ly, ny);
+            const unsigned xx = wrapc(x0 - 2 + lx, nx, smx), yy = wrapc(y0 - 2 + ly, ny, smy);
             dst[q] = phif[zo + yy * nx + xx];
         }
     };
@@ -134,21 +139,23 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
     // zz-1..zz+1 (read), zz+3 (written: a fifth slot); mu planes zz-1..zz+1.
     constexpr int PPT = (PA + TX3 * TY3 - 1) / (TX3 * TY3);
     const unsigned xw = col_ok ? (unsigned)x : 0, yw = col_ok ? (unsigned)y : 0;
+    Nb b = make_nb(xw, yw, z0, nx, ny, nz);
     for (int zz = z0; zz < zend; ++zz) {
         T pre[PPT];
         {
-            const unsigned zo = (unsigned)wrapi(zz + 3, nz) * plane;
+            const unsigned zo = (unsigned)wrapc(zz + 3, nz, smz) * plane;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const int q = tid + k * TX3 * TY3;
                 if (q < PA) {
-                    const unsigned xx = wrapi(x0 - 2 + q % PX, nx), yy = wrapi(y0 - 2 + q / PX, ny);
+                    const unsigned xx = wrapc(x0 - 2 + q % PX, nx, smx),
+                                   yy = wrapc(y0 - 2 + q / PX, ny, smy);
                     pre[k] = phif[zo + yy * nx + xx];
                 }
             }
         }
         if (col_ok) {
-        const Nb b = make_nb(xw, yw, zz, nx, ny, nz);
+        nb_plane(b, zz, nx, ny, nz);
         const unsigned n = b.at(0, 0, 0);
         T fv[19], gv[19];
 #pragma unroll
@@ -417,8 +424,8 @@ cudaError_t launch3(const void *params, const PassArgs &a, const LaunchShape &s,
                     cudaStream_t st)
 {
     const StepParams<T> &P = *static_cast<const StepParams<T> *>(params);
-    const unsigned nb = (unsigned)((P.N + 255) / 256);
-    d3q19_phi_kernel<T><<<nb, 256, 0, st>>>(P, static_cast<const T *>(a.f_src), static_cast<T *>(phi));
+    const dim3 pg((P.nx + PHI_TX - 1) / PHI_TX, P.ny, P.nz);
+    d3q19_phi_kernel<T><<<pg, PHI_TX, 0, st>>>(P, static_cast<const T *>(a.f_src), static_cast<T *>(phi));
     dim3 grid(s.grid_x, s.grid_y, s.nblocks / (s.grid_x * s.grid_y)), block(TX3, TY3);
     d3q19_pass_kernel<T, PASS><<<grid, block, 0, st>>>(P, a, static_cast<const T *>(phi), s.rows);
     return cudaGetLastError();

@@ -79,16 +79,18 @@ __host__ __device__ inline OffBuf off_view(const void *fbuf, const void *gbuf, l
 // phi(x) = sum_i f_i(x): the rest value phi(x) - (1 - w0) alpha mu(x) + s_f h_0(x)
 // and the moving values w_i alpha mu(x - c_i) + s_f h_i(x - c_i), i.e.
 // phi(x) + alpha sum_{i != 0} w_i (mu(x - c_i) - mu(x)) + s_f sum_i h_i(x - c_i).
+// grid (ceil(nx / PHI_TX), ny, nz): one thread per node of a row
+constexpr int PHI_TX = 128;
 template <class C>
-__global__ void d3q19_off_phi_kernel(const StepParams<float> P, const OffBuf src,
-                                     float *__restrict__ phi)
+__global__ void __launch_bounds__(PHI_TX)
+    d3q19_off_phi_kernel(const StepParams<float> P, const OffBuf src, float *__restrict__ phi)
 {
-    const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned N = (unsigned)P.N;
-    if (n >= N) return;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    const int x = blockIdx.x * PHI_TX + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const unsigned N = (unsigned)P.N;
     const Nb b = make_nb(x, y, z, nx, ny, nz);
+    const unsigned n = b.at(0, 0, 0);
     const float *__restrict__ mu = src.M + N;
     const float mux = __ldg(mu + n);
     float sh = C::dec(__ldg(src.h + n)), dfa = 0.0f, ded = 0.0f;
@@ -145,12 +147,14 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
     auto mslot = [&](int zz) { return (zz - z0 + 1) % RM; };
     auto qslot = [&](int zz) { return (zz - z0 + 1) % RQ; };
 
+    // grids narrower than a tile plus halo wrap by division (uniform flags)
+    const bool smx = nx < PX + 2, smy = ny < PY + 2, smz = nz < 8;
     auto load_phi_plane = [&](int zz) {
         float *d = phs + pslot(zz) * PA;
-        const unsigned zo = (unsigned)wrapi(zz, nz) * plane;
+        const unsigned zo = (unsigned)wrapc(zz, nz, smz) * plane;
         for (int q = tid; q < PA; q += TX3 * TY3) {
             const int lx = q % PX, ly = q / PX;
-            const unsigned xx = wrapi(x0 - 2 + lx, nx), yy = wrapi(y0 - 2 + ly, ny);
+            const unsigned xx = wrapc(x0 - 2 + lx, nx, smx), yy = wrapc(y0 - 2 + ly, ny, smy);
             d[q] = phif[zo + yy * nx + xx];
         }
     };
@@ -184,8 +188,8 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
         qb[slot * MA + q] = make_float2(rho * m6[5], 4.5f / rho);
     };
     auto macro_node = [&](int zz, int q) {
-        const unsigned m = (unsigned)wrapi(zz, nz) * plane + (unsigned)wrapi(y0 - 1 + q / MX, ny) * nx +
-                           wrapi(x0 - 1 + q % MX, nx);
+        const unsigned m = (unsigned)wrapc(zz, nz, smz) * plane +
+                           (unsigned)wrapc(y0 - 1 + q / MX, ny, smy) * nx + wrapc(x0 - 1 + q % MX, nx, smx);
         return m;
     };
     auto macro_plane = [&](int zz) {
@@ -230,15 +234,17 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
     constexpr int PPT = (PA + TX3 * TY3 - 1) / (TX3 * TY3);
     constexpr int MPT = (MA + TX3 * TY3 - 1) / (TX3 * TY3);
     const unsigned xw = col_ok ? (unsigned)x : 0, yw = col_ok ? (unsigned)y : 0;
+    Nb b = make_nb(xw, yw, z0, nx, ny, nz);
     for (int zz = z0; zz < zend; ++zz) {
         float pre[PPT], mre[MPT][6];
         {
-            const unsigned zo = (unsigned)wrapi(zz + 3, nz) * plane;
+            const unsigned zo = (unsigned)wrapc(zz + 3, nz, smz) * plane;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const int q = tid + k * TX3 * TY3;
                 if (q < PA) {
-                    const unsigned xx = wrapi(x0 - 2 + q % PX, nx), yy = wrapi(y0 - 2 + q / PX, ny);
+                    const unsigned xx = wrapc(x0 - 2 + q % PX, nx, smx),
+                                   yy = wrapc(y0 - 2 + q / PX, ny, smy);
                     pre[k] = phif[zo + yy * nx + xx];
                 }
             }
@@ -253,8 +259,7 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
             }
         }
         if (col_ok) {
-
-        const Nb b = make_nb(xw, yw, zz, nx, ny, nz);
+        nb_plane(b, zz, nx, ny, nz);
         const unsigned n = b.at(0, 0, 0);
         unsigned short hr[19], kr[19];
 #pragma unroll
@@ -646,8 +651,8 @@ cudaError_t launch_off(const StepParams<float> &P, const PassArgs &a, const Laun
                        float *phi, const float *target, cudaStream_t st)
 {
     const OffBuf src = off_view(a.f_src, a.g_src, P.N), dst = off_view(a.f_dst, a.g_dst, P.N);
-    const unsigned nb = (unsigned)((P.N + 255) / 256);
-    d3q19_off_phi_kernel<C><<<nb, 256, 0, st>>>(P, src, phi);
+    const dim3 pg((P.nx + PHI_TX - 1) / PHI_TX, P.ny, P.nz);
+    d3q19_off_phi_kernel<C><<<pg, PHI_TX, 0, st>>>(P, src, phi);
     dim3 grid(s.grid_x, s.grid_y, s.nblocks / (s.grid_x * s.grid_y)), block(TX3, TY3);
     d3q19_off_pass_kernel<C, PASS><<<grid, block, 0, st>>>(P, a, src, dst, target, phi, s.rows);
     return cudaGetLastError();
