@@ -228,12 +228,14 @@ int lbm_set_state(lbm_ctx *ctx, const double *f, const double *g,
 
 /* Checkpoint to / restore from a host buffer in the library's own format
  * (header, which also records the FP32 equilibrium shift, then the raw
- * device state at the context's precision: f, g, S_prev
- * in the storage layout described at lbm_diagnostics_noalloc; for the offset
- * precisions f is the Q offset arrays (u16), the D + 3 FP32 macro arrays
- * (phi, mu, p, u), each padded to 256 bytes, and the two FP32 scales padded
- * to 256 bytes, and g is the Q offset arrays; a restore is bit-exact).  lbm_save with buf == NULL stores the required size in *bytes.
- * lbm_load checks that grid, lattice and precision match.  Errors:
+ * device state at the context's precision: f, g, S_prev in the storage
+ * layout described at lbm_diagnostics_noalloc; for the offset precisions f
+ * is the Q offset arrays (u16), then D + 4 FP32 arrays (the macros phi, mu,
+ * p, u and the offset-free part of the next step's phi sum), then the two
+ * FP32 scales, each part padded to 256 bytes, and g is the Q offset arrays;
+ * a restore is bit-exact).  lbm_save with buf == NULL stores the required
+ * size in *bytes.  lbm_load checks that grid, lattice and precision match.
+ * Errors:
  * INVALID_ARG (size or header mismatch), STATE, CUDA. */
 int lbm_save(lbm_ctx *ctx, void *buf, size_t *bytes);
 int lbm_load(lbm_ctx *ctx, const void *buf, size_t bytes);

@@ -12,8 +12,11 @@
 // together with the macros of y - c_i.
 //
 // Storage of one parity of the double buffer (offset_layout):
-//   f buffer: h[19][N] (u16) | M[6][N] (FP32: phi, mu, p, ux, uy, uz) | s_f, s_g
+//   f buffer: h[19][N] (u16) | M[7][N] (FP32: phi, mu, p, ux, uy, uz, B) | s_f, s_g
 //   g buffer: k[19][N] (u16)
+// B = phi + alpha sum_{i != 0} w_i (mu(x + c_i) - mu(x)) is the part of the
+// next step's phi(x) that does not depend on the offsets; the step writes it
+// from its mu ring, so the next phi pass streams B and the offsets only.
 // The rest population keeps phi exactly the way the FP32 path's compensated
 // pair does: phi (FP32) in M is its high word, and the rounding residual of
 // phi is folded into the rest offset h_0.
@@ -28,8 +31,8 @@
 // A step is two passes, as in the FP32 D3Q19 path: d3q19_off_phi_kernel
 // writes phi from the pulled populations, then d3q19_off_pass_kernel marches
 // down z with phi, mu and the macro planes of the source state in
-// shared-memory rings.  HBM traffic per node: 38 + 8 + 4 B (pass 1) and
-// 2 x (38 + 38 + 24 + 4) + 4 B (pass 2).
+// shared-memory rings.  HBM traffic per node: 38 + 4 + 4 B (pass 1) and
+// 38 + 38 + 24 + 4 + 4 B read, 38 + 38 + 28 + 4 B written (pass 2).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
@@ -63,13 +66,13 @@ struct CodecBF16 {
 // views of one parity of the offset storage
 struct OffBuf {
     unsigned short *h, *k;  // f and g offsets [19][N]
-    float *M;               // macros [6][N]
+    float *M;               // macros [7][N] (phi, mu, p, u, B)
     float *sc;              // s_f, s_g
 };
 
 __host__ __device__ inline OffBuf off_view(const void *fbuf, const void *gbuf, long long N)
 {
-    const OffsetLayout L = offset_layout(N, 19, 3);
+    const OffsetLayout L = offset_layout(N, 19, 3);  // 3 + 4 FP32 arrays
     char *fb = (char *)fbuf;
     return OffBuf{(unsigned short *)fb, (unsigned short *)gbuf, (float *)(fb + L.mac_off),
                   (float *)(fb + L.sc_off)};
@@ -78,7 +81,7 @@ __host__ __device__ inline OffBuf off_view(const void *fbuf, const void *gbuf, l
 // ------------------------------------------------------------------ pass 1
 // phi(x) = sum_i f_i(x): the rest value phi(x) - (1 - w0) alpha mu(x) + s_f h_0(x)
 // and the moving values w_i alpha mu(x - c_i) + s_f h_i(x - c_i), i.e.
-// phi(x) + alpha sum_{i != 0} w_i (mu(x - c_i) - mu(x)) + s_f sum_i h_i(x - c_i).
+// B(x) + s_f sum_i h_i(x - c_i) with B = phi + alpha sum_{i != 0} w_i (mu(x - c_i) - mu(x)).
 // grid (ceil(nx / PHI_TX), ny, nz): one thread per node of a row
 constexpr int PHI_TX = 128;
 template <class C>
@@ -91,20 +94,31 @@ __global__ void __launch_bounds__(PHI_TX)
     const unsigned N = (unsigned)P.N;
     const Nb b = make_nb(x, y, z, nx, ny, nz);
     const unsigned n = b.at(0, 0, 0);
-    const float *__restrict__ mu = src.M + N;
-    const float mux = __ldg(mu + n);
-    float sh = C::dec(__ldg(src.h + n)), dfa = 0.0f, ded = 0.0f;
+    float sh = C::dec(__ldg(src.h + n));
 #pragma unroll
+    for (int i = 1; i < 19; ++i) sh += C::dec(__ldg(src.h + (i * N + b.at(-c3x(i), -c3y(i), -c3z(i)))));
+    phi[n] = __ldg(src.M + 6 * N + n) + __ldg(src.sc) * sh;
+}
+
+// B(x) from stored macros (after an initial condition or a state exchange)
+__global__ void d3q19_off_prep_k(const StepParams<float> P, OffBuf o)
+{
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int x = blockIdx.x * PHI_TX + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const unsigned N = (unsigned)P.N;
+    const Nb b = make_nb(x, y, z, nx, ny, nz);
+    const unsigned n = b.at(0, 0, 0);
+    const float *mu = o.M + N, mux = mu[n];
+    float dfa = 0.0f, ded = 0.0f;
     for (int i = 1; i < 19; ++i) {
-        const unsigned m = b.at(-c3x(i), -c3y(i), -c3z(i));
-        sh += C::dec(__ldg(src.h + (i * N + m)));
+        const float d = mu[b.at(c3x(i), c3y(i), c3z(i))] - mux;
         if (i <= 6)
-            dfa += __ldg(mu + m) - mux;
+            dfa += d;
         else
-            ded += __ldg(mu + m) - mux;
+            ded += d;
     }
-    const float lo = P.alpha * (1.0f / 18.0f * dfa + 1.0f / 36.0f * ded) + __ldg(src.sc) * sh;
-    phi[n] = __ldg(src.M + n) + lo;
+    o.M[6 * N + n] = o.M[n] + P.alpha * (1.0f / 18.0f * dfa + 1.0f / 36.0f * ded);
 }
 
 // ------------------------------------------------------------------ pass 2
@@ -368,6 +382,19 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
             __stcs(dst.M + 3 * N + n, u[0]);
             __stcs(dst.M + 4 * N + n, u[1]);
             __stcs(dst.M + 5 * N + n, u[2]);
+            {
+                // B = phi + alpha sum_{i != 0} w_i (mu(x + c_i) - mu(x)) from the mu ring
+                const float *m0 = mz, *mm = mus + mslot(zz - 1) * MA, *mp = mus + mslot(zz + 1) * MA;
+                const float fa = (m0[cm + 1] - mu) + (m0[cm - 1] - mu) + (m0[cm + MX] - mu) +
+                                 (m0[cm - MX] - mu) + (mp[cm] - mu) + (mm[cm] - mu);
+                const float ed = ((m0[cm + MX + 1] - mu) + (m0[cm + MX - 1] - mu) +
+                                  (m0[cm - MX + 1] - mu) + (m0[cm - MX - 1] - mu)) +
+                                 ((mp[cm + 1] - mu) + (mp[cm - 1] - mu) + (mm[cm + 1] - mu) +
+                                  (mm[cm - 1] - mu)) +
+                                 ((mp[cm + MX] - mu) + (mp[cm - MX] - mu) + (mm[cm + MX] - mu) +
+                                  (mm[cm - MX] - mu));
+                __stcs(dst.M + 6 * N + n, phi + P.alpha * ((1.0f / 18.0f) * fa + (1.0f / 36.0f) * ed));
+            }
             // CH population (Eqs. BGK, F_i): offset = (f - f^eq)(1 - 1/tau_f) + F_i,
             // b = -5/2, -1, 1/2; the rest offset also carries the residual r of phi
             const float Sh = 1.5f * S - 0.5f * Sprev;
@@ -705,6 +732,7 @@ cudaError_t d3q19_off_init(int codec, const void *params64, const void *params32
     else
         d3q19_off_init_k<CodecBF16><<<nb, 256, 0, st>>>(Pd, P, phi0, mu_tmp, o, (float *)S,
                                                         target_host[0], target_host[1]);
+    d3q19_off_prep_k<<<dim3((P.nx + PHI_TX - 1) / PHI_TX, P.ny, P.nz), PHI_TX, 0, st>>>(P, o);
     return cudaGetLastError();
 }
 
@@ -734,6 +762,7 @@ cudaError_t d3q19_off_set_state(int codec, const void *params32, void *f, void *
     else
         d3q19_off_set_k<CodecBF16><<<nb, 256, 0, st>>>(P, o, (float *)S, fi, gi, Si,
                                                        target_host[0], target_host[1]);
+    d3q19_off_prep_k<<<dim3((P.nx + PHI_TX - 1) / PHI_TX, P.ny, P.nz), PHI_TX, 0, st>>>(P, o);
     return cudaGetLastError();
 }
 

@@ -117,7 +117,8 @@ cudaError_t d3q19_init_mu_fp64(const void *params, const double *phi0, double *m
 
 // Populations stored as 16-bit offsets from their equilibria
 // (kernels_d3q19_off.cu).  One parity of the state: the f buffer holds the
-// Q offset arrays (u16), then D + 3 FP32 macro arrays (phi, mu, p, u), then
+// Q offset arrays (u16), then D + 4 FP32 arrays (phi, mu, p, u, and the
+// part of the next step's phi that does not depend on the offsets), then
 // the two FP32 scales (s_f, s_g); the g buffer holds the Q offset arrays.
 enum : int { OFFSET_F16 = 0, OFFSET_BF16 = 1 };
 constexpr float OFFSET_SCALE_FLOOR = 1.0f / 65536.0f;  // 2^-16
@@ -130,7 +131,7 @@ __host__ __device__ inline OffsetLayout offset_layout(long long N, int Q, int D)
     const size_t n = (size_t)N, a = 256;
     OffsetLayout L;
     L.mac_off = ((size_t)Q * n * 2 + a - 1) / a * a;
-    L.sc_off = L.mac_off + (((size_t)(D + 3) * n * 4 + a - 1) / a * a);
+    L.sc_off = L.mac_off + (((size_t)(D + 4) * n * 4 + a - 1) / a * a);
     L.fbytes = L.sc_off + a;
     L.gbytes = (size_t)Q * n * 2;
     return L;
