@@ -320,6 +320,30 @@ def run_native(args, rank, world, local_rank):
 
     if rank != 0:
         return
+    # spurious velocity and phi of the e2e run's final state against the FP64
+    # path (in parity with the FP64 oracle) after the same steps (not timed)
+    accuracy = None
+    if prec == "fp32":
+        ref = Batch(cases, precision="fp64", stream=stream.cuda_stream)
+        for i in range(len(ref)):
+            ref.case(i).init_phi(phi_d)
+        ref.step(args.steps)
+        accuracy = {"steps": args.steps, "max_u_fp32": 0.0, "max_u_fp64": 0.0,
+                    "max_abs_u_diff_vs_fp64": 0.0, "max_abs_phi_diff_vs_fp64": 0.0,
+                    "reference": "FP64 GPU path (parity with the FP64 oracle at 1e-12), same "
+                                 "phi0 and steps, both density ratios"}
+        for i, o in enumerate(outs):
+            m = ref.case(i).moments()
+            u64 = m["u"].reshape(2, -1)
+            u32 = o["u"].reshape(2, -1)
+            accuracy["max_u_fp32"] = max(accuracy["max_u_fp32"], float(np.hypot(*u32).max()))
+            accuracy["max_u_fp64"] = max(accuracy["max_u_fp64"], float(np.hypot(*u64).max()))
+            accuracy["max_abs_u_diff_vs_fp64"] = max(accuracy["max_abs_u_diff_vs_fp64"],
+                                                     float(np.abs(u32 - u64).max()))
+            accuracy["max_abs_phi_diff_vs_fp64"] = max(
+                accuracy["max_abs_phi_diff_vs_fp64"],
+                float(np.abs(o["phi"] - m["phi"].reshape(-1)).max()))
+        ref.close()
     peaks, src = measured_peaks()
     bpn = BYTES_PER_NODE[prec]
     achieved = bpn * nodes / kernel_s / 1e9
@@ -348,6 +372,7 @@ def run_native(args, rank, world, local_rank):
                        "lbm_batch_step (autotune on the first call) in chunks of diag_every steps each followed "
                        "by lbm_diagnostics (device-to-host read) of both grids, final "
                        "lbm_moments of both grids to host"},
+        "accuracy": accuracy,
         "gpu_launches": args.steps + 4 * len(plan),
         "clocks": clk.summary(t_start, t_end),
         "wall_s_timed_region": t_wall,

@@ -59,6 +59,16 @@ struct Nb {
     __device__ unsigned at(int dx, int dy, int dz) const { return zs[dz + 1] + ys[dy + 1] + xs[dx + 1]; }
 };
 
+// per-thread asynchronous 4-byte copy global -> shared; a thread's own
+// copies are visible to it after cp_wait_all
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // x, y, z in [0, n): the neighbours at -1..1 wrap without a division
 __device__ __forceinline__ void nb_plane(Nb &b, int z, int nx, int ny, int nz)
 {

@@ -133,9 +133,11 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
 {
     constexpr int PX = TX3 + 4, PY = TY3 + 4, PA = PX * PY;  // phi plane (halo 2)
     constexpr int MX = TX3 + 2, MY = TY3 + 2, MA = MX * MY;  // mu / macro plane (halo 1)
-    constexpr int RP = 5, RM = 3, RQ = 4;
+    constexpr int RP = 5, RM = 3, RQ = 3;
     __shared__ float phs[RP * PA];
     __shared__ float mus[RM * MA];
+    // the source macros of the plane two ahead, copied while a plane is updated
+    __shared__ float mraw[6 * MA];
     // per source node: {alpha mu, A = 3p - 3/2 rho |u|^2, rho ux, rho uy} and
     // {rho uz, 9 / (2 rho)}: g^eq_i = w_i (A + 3 c.j + (9/2)(c.j)^2 / rho)
     __shared__ float4 qa[RQ * MA];
@@ -240,48 +242,42 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
     mu_plane(z0 + 1);
     __syncthreads();
 
-    // Plane zz + 3 of phi and plane zz + 2 of the source macros travel
-    // through registers while plane zz is updated, so their loads overlap the
-    // node's own pulls.  Ring use during the update of plane zz: phi zz-1..zz+1
-    // (read) and zz+3 (written); mu zz-1..zz+1; macros zz-1..zz+1 (read) and
-    // zz+2 (written: a fourth slot).
-    constexpr int PPT = (PA + TX3 * TY3 - 1) / (TX3 * TY3);
-    constexpr int MPT = (MA + TX3 * TY3 - 1) / (TX3 * TY3);
+    // Plane zz + 3 of phi (into its ring slot) and the raw source macros of
+    // plane zz + 2 (into mraw) are copied asynchronously while plane zz is
+    // updated, so their loads overlap the node's own pulls and hold no
+    // registers.  Ring use during the update of plane zz: phi zz-1..zz+1
+    // (read) and zz+3 (being written); mu and macros zz-1..zz+1; once every
+    // thread is past the update, macro plane zz+2 and mu plane zz+2 take the
+    // slots of zz-1.
     const unsigned xw = col_ok ? (unsigned)x : 0, yw = col_ok ? (unsigned)y : 0;
     Nb b = make_nb(xw, yw, z0, nx, ny, nz);
     for (int zz = z0; zz < zend; ++zz) {
-        float pre[PPT], mre[MPT][6];
         {
             const unsigned zo = (unsigned)wrapc(zz + 3, nz, smz) * plane;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const int q = tid + k * TX3 * TY3;
-                if (q < PA) {
-                    const unsigned xx = wrapc(x0 - 2 + q % PX, nx, smx),
-                                   yy = wrapc(y0 - 2 + q / PX, ny, smy);
-                    pre[k] = phif[zo + yy * nx + xx];
-                }
+            float *d = phs + pslot(zz + 3) * PA;
+            for (int q = tid; q < PA; q += TX3 * TY3) {
+                const unsigned xx = wrapc(x0 - 2 + q % PX, nx, smx), yy = wrapc(y0 - 2 + q / PX, ny, smy);
+                cp_async4(d + q, phif + (zo + yy * nx + xx));
             }
+            for (int q = tid; q < MA; q += TX3 * TY3) {
+                const unsigned m = macro_node(zz + 2, q);
 #pragma unroll
-            for (int k = 0; k < MPT; ++k) {
-                const int q = tid + k * TX3 * TY3;
-                if (q < MA) {
-                    const unsigned m = macro_node(zz + 2, q);
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) mre[k][c] = __ldg(src.M + c * N + m);
-                }
+                for (int c = 0; c < 6; ++c) cp_async4(mraw + c * MA + q, src.M + ((size_t)c * N + m));
             }
+            cp_commit();
         }
         if (col_ok) {
         nb_plane(b, zz, nx, ny, nz);
         const unsigned n = b.at(0, 0, 0);
-        unsigned short hr[19], kr[19];
+        // the two 16-bit offsets of direction i share one register
+        unsigned hk[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const unsigned s = b.at(-c3x(i), -c3y(i), -c3z(i));
-            hr[i] = __ldg(src.h + (i * N + s));
-            kr[i] = __ldg(src.k + (i * N + s));
+            hk[i] = (unsigned)__ldg(src.h + (i * N + s)) | ((unsigned)__ldg(src.k + (i * N + s)) << 16);
         }
+        auto hr = [&](int i) { return (unsigned short)(hk[i] & 0xffffu); };
+        auto kr = [&](int i) { return (unsigned short)(hk[i] >> 16); };
         float Sprev = 0.0f;
         if (PASS & (PASS_STATE | PASS_DIAG)) Sprev = __ldcs(static_cast<const float *>(a.S) + n);
         const float phi_hi = __ldg(src.M + n), p_own = __ldg(src.M + 2 * N + n);
@@ -292,8 +288,8 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
         float flo;  // rest population minus its high word phi_hi
         {
             const float4 A0 = qa[qslot(zz) * MA + cq];
-            flo = -(2.0f / 3.0f) * A0.x + s_f * C::dec(hr[0]);
-            gv[0] = (1.0f / 3.0f) * A0.y - 3.0f * p_own + s_g * C::dec(kr[0]);
+            flo = -(2.0f / 3.0f) * A0.x + s_f * C::dec(hr(0));
+            gv[0] = (1.0f / 3.0f) * A0.y - 3.0f * p_own + s_g * C::dec(kr(0));
             fv[0] = 0.0f;
         }
 #pragma unroll
@@ -302,12 +298,12 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
             const float4 A = qa[c];
             const float2 B = qb[c];
             const float w = (float)w3(i);
-            fv[i] = w * A.x + s_f * C::dec(hr[i]);
+            fv[i] = w * A.x + s_f * C::dec(hr(i));
             float cj = 0.0f;
             if (c3x(i)) cj += (float)c3x(i) * A.z;
             if (c3y(i)) cj += (float)c3y(i) * A.w;
             if (c3z(i)) cj += (float)c3z(i) * B.x;
-            gv[i] = w * (A.y + cj * (3.0f + B.y * cj)) + s_g * C::dec(kr[i]);
+            gv[i] = w * (A.y + cj * (3.0f + B.y * cj)) + s_g * C::dec(kr(i));
         }
 
         float snz = 0.0f, sg = 0.0f;
@@ -428,17 +424,14 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_off_pass_kernel(const StepPara
             }
         }
         }  // col_ok
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const int q = tid + k * TX3 * TY3;
-            if (q < PA) phs[pslot(zz + 3) * PA + q] = pre[k];
-        }
-#pragma unroll
-        for (int k = 0; k < MPT; ++k) {
-            const int q = tid + k * TX3 * TY3;
-            if (q < MA) put_macros(qslot(zz + 2), q, mre[k]);
-        }
+        cp_wait_all();
         __syncthreads();
+        for (int q = tid; q < MA; q += TX3 * TY3) {  // own copies: no barrier needed
+            float m6[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) m6[c] = mraw[c * MA + q];
+            put_macros(qslot(zz + 2), q, m6);
+        }
         mu_plane(zz + 2);
         __syncthreads();
     }

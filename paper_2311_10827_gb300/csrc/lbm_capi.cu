@@ -101,8 +101,9 @@ int validate(const lbm_grid *g, int lattice, const lbm_params *p)
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_ERR_INVALID_ARG;
     if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_ERR_INVALID_ARG;
     if (lattice == LBM_D2Q9 && g->nz != 1) return LBM_ERR_INVALID_ARG;
-    // population offsets are 32-bit in the kernels
-    if ((long long)g->nx * g->ny * g->nz * 19 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
+    // population offsets are 32-bit in the kernels (up to 20 arrays: the 19
+    // D3Q19 populations and the FP32 rest population's low word)
+    if ((long long)g->nx * g->ny * g->nz * 20 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p->W) || !isfinite(p->sigma) || p->sigma < 0.0) return LBM_ERR_INVALID_ARG;
     if (!finite_pos(p->M)) return LBM_ERR_INVALID_ARG;
     if (p->tau_f == 0.0) {
