@@ -322,8 +322,9 @@ def run_native(args, rank, world, local_rank):
     # spurious velocity and phi of the e2e run's final state against the FP64
     # path (in parity with the FP64 oracle) after the same steps (not timed)
     accuracy = None
-    if prec == "fp32":
+    if prec == "fp32" and not args.no_accuracy:
         ref = Batch(cases, precision="fp64", stream=stream.cuda_stream)
+        ref.set_shape(width, rows)  # no tuning
         for i in range(len(ref)):
             ref.case(i).init_phi(phi_d)
         ref.step(args.steps)
@@ -635,6 +636,8 @@ def main():
                     help="f16off / bf16off: 16-bit offset storage (coalescence3d only)")
     ap.add_argument("--diag-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP64 comparison run after the timed region (profiling)")
     ap.add_argument("--tile", default="", help="WxR: fixed batch tile shape instead of the "
                     "autotuner (profiling commands use the shape the tuner picked)")
     ap.add_argument("--workload", choices=["droplet1024", "ensemble", "coalescence3d", "adjoint"],

@@ -21,7 +21,9 @@
 // Row tiles march in alternating directions (even tiles down, odd tiles up),
 // so two neighbouring tiles reach their shared boundary rows at the same
 // time and the y-halo rows are served from L2 instead of being re-read from
-// HBM.
+// HBM; every other step reverses all directions, so a step starts on the
+// rows the previous step wrote last (still in L2 when a step's data is
+// comparable to the L2 size).
 //
 // FP32 storage keeps the rest population f_0 (~phi, O(1)) as a compensated
 // pair hi + lo of FP32 words (lo in population slot 9): its per-step change
@@ -136,10 +138,13 @@ __device__ __forceinline__ T sum_moving(const T v[9])
     return ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
 }
 
+// Stores of the step's outputs are ordinary write-back stores: the next step
+// reads them, and with the march reversed every step the rows a tile wrote
+// last -- the ones most likely still in L2 -- are read first.
 template <typename T>
 __device__ __forceinline__ void st_stream(T *p, T v)
 {
-    __stcs(p, v);
+    *p = v;
 }
 
 __device__ __forceinline__ void warp_reduce(double &sum0, double &sum1, double &mx, double &mn,
@@ -206,12 +211,13 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     const int jM = tx == 0 ? 0 : TX + 1;
 
     // FP32: equilibrium shift of the source buffer and of the writes (a uniform
-    // shift of mu in f^eq; phi, the moments and the stencils do not see it)
+    // shift of mu in f^eq; phi, the moments and the stencils do not see it, so
+    // only a time step reads it)
     T a_src = T(0), a_dst = T(0);
-    if (REST_PAIR) {
+    if (REST_PAIR && (PASS & PASS_STATE)) {
         a_src = *a.eqs_src;
         a_dst = *a.eqs_target;
-        if ((PASS & PASS_STATE) && x0 == 0 && y0 == 0 && lin == 0) *a.eqs_dst = a_dst;
+        if (x0 == 0 && y0 == 0 && lin == 0) *a.eqs_dst = a_dst;
     }
 
     // m(row) = dir (row - first) is the march coordinate, >= -2 for every row used
@@ -539,8 +545,11 @@ __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS, TX>::ctas))
     d2q9_pass_kernel(const StepParams<T> P, PassArgs a, int rows)
 {
     const int y0 = blockIdx.y * rows;
-    d2q9_tile<T, TX, PASS>(P, a, blockIdx.x * TX, y0, min(y0 + rows, P.ny),
-                           (blockIdx.y & 1) ? -1 : 1, blockIdx.y * gridDim.x + blockIdx.x);
+    // march direction: alternating between neighbouring row tiles, and
+    // reversed on every other step
+    const int dir = ((blockIdx.y & 1) ? -1 : 1) * (a.flip ? -1 : 1);
+    d2q9_tile<T, TX, PASS>(P, a, blockIdx.x * TX, y0, min(y0 + rows, P.ny), dir,
+                           blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Batched: CTA k runs tile k of a flat tile table over many independent grids
@@ -567,7 +576,7 @@ __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS, TX>::ctas))
     a.eqs_src = c.eqs + parity;
     a.eqs_dst = c.eqs + (parity ^ 1);
     a.eqs_target = c.eqs + 2;
-    d2q9_tile<T, TX, PASS>(P, a, t.x0, t.y0, t.yend, t.dir, blockIdx.x);
+    d2q9_tile<T, TX, PASS>(P, a, t.x0, t.y0, t.yend, parity ? -t.dir : t.dir, blockIdx.x);
 }
 
 // ------------------------------------------------------------ initial state

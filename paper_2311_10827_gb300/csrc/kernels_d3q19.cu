@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(TX3 *TY3) d3q19_pass_kernel(const StepParams<T
     double d_phi = 0.0, d_E = 0.0, d_u2 = 0.0, d_mumin = DBL_MAX, d_mumax = -DBL_MAX,
            d_bud = 0.0, d_bad = 0.0;
 
-    // FP32: equilibrium shift of the source buffer and of the writes
+    // FP32: equilibrium shift of the source buffer and of the writes (only a
+    // time step reads it)
     T a_src = T(0), a_dst = T(0);
-    if (sizeof(T) == 4) {
+    if (sizeof(T) == 4 && (PASS & PASS_STATE)) {
         a_src = *a.eqs_src;
         a_dst = *a.eqs_target;
-        if ((PASS & PASS_STATE) && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
-            *a.eqs_dst = a_dst;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) *a.eqs_dst = a_dst;
     }
 
     for (int q = 0; q < 5; ++q) load_phi_plane(z0 - 2 + q);

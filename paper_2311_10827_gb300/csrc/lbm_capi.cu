@@ -182,6 +182,7 @@ int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p
     a.eqs_src = ctx->eqs + ctx->cur;
     a.eqs_dst = ctx->eqs + (ctx->cur ^ 1);
     a.eqs_target = ctx->eqs + 2;
+    a.flip = ctx->cur;
     if (ctx->codec >= 0)
         CK(d3q19_off_pass(ctx->codec, pass, &ctx->pf, a, ctx->shape, ctx->phiw, ctx->scw, st));
     else if (ctx->lattice == LBM_D3Q19)

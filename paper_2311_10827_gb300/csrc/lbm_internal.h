@@ -48,6 +48,7 @@ struct PassArgs {
     const float *eqs_src;
     float *eqs_dst;
     const float *eqs_target;
+    int flip;  // step parity: D2Q9 row tiles reverse their march direction on odd steps
 };
 
 // FP32 storage holds the f populations shifted by a uniform equilibrium
