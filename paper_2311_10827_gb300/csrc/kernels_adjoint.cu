@@ -86,9 +86,11 @@ __device__ __forceinline__ void block_add(double v, double *dst)
     }
 }
 
-// lambda_phi, lambda_mu, lambda_grad phi, lambda_grad mu and dL/d(1/tau_f)
+// lambda_phi, lambda_mu, lambda_grad phi, lambda_grad mu and dL/d(1/tau_f);
+// the FP32 form fits 80 registers (3 resident CTAs per SM instead of 2: the
+// kernel waits on gathered loads, so more warps help)
 template <typename T, typename R>
-__global__ void adj_local(const StepParams<double> P, AdjGeom geo, const T *__restrict__ f,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) adj_local(const StepParams<double> P, AdjGeom geo, const T *__restrict__ f,
                           const T *__restrict__ g, int rest_pair, const double *__restrict__ phi,
                           const double *__restrict__ mu, const double *__restrict__ pf,
                           const double *__restrict__ uf, const R *__restrict__ lf_in,

@@ -192,6 +192,36 @@ int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p
     return LBM_OK;
 }
 
+// D2Q9 pass over a state held in a snapshot (f | g | S contiguous, the
+// adjoint's layout) instead of the context's buffers; a time step writes the
+// next state into `next` (same layout).  The equilibrium shift stays at the
+// context's (constant while an adjoint recorder is attached).
+int run_pass_snap(lbm_ctx *ctx, int pass, const char *snap, char *next, double *o_phi,
+                  double *o_p, double *o_u, double *o_mu)
+{
+    const size_t fb = ctx->fbytes, gb = ctx->gbytes;
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.f_src = snap;
+    a.g_src = snap + fb;
+    a.S = (void *)(snap + fb + gb);
+    if (next) {
+        a.f_dst = next;
+        a.g_dst = next + fb;
+        a.S_out = next + fb + gb;
+    }
+    a.out_phi = o_phi;
+    a.out_p = o_p;
+    a.out_u = o_u;
+    a.out_mu = o_mu;
+    a.partials = ctx->partials;
+    a.eqs_src = ctx->eqs + ctx->cur;
+    a.eqs_dst = ctx->eqs + (ctx->cur ^ 1);
+    a.eqs_target = ctx->eqs + ctx->cur;
+    CK(d2q9_pass(ctx->prm.precision, pass, params_ptr(ctx), a, ctx->shape, ctx->stream));
+    return LBM_OK;
+}
+
 // offset storage: new target scales from the current state
 int refresh_scales(lbm_ctx *ctx, cudaStream_t st)
 {
@@ -1344,18 +1374,20 @@ int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, d
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int t0 = sgi * a->K;
         const int len = a->nsteps - t0 < a->K ? a->nsteps - t0 : a->K;
-        // recompute the segment forward, keeping every state
-        if (int rc = restore(ctx, a->ckpt + (size_t)sgi * a->snap, t0)) return rc;
-        for (int j = 0; j < len; ++j) {
-            if (int rc = snapshot(ctx, a->seg + (size_t)j * a->snap, a->snap)) return rc;
-            if (j + 1 < len)
-                if (int rc = lbm_step(ctx, 1)) return rc;
-        }
-        // reverse through it
+        // recompute the segment forward from its checkpoint, each step writing
+        // straight into the next state slot of the segment
+        CK(cudaMemcpyAsync(a->seg, a->ckpt + (size_t)sgi * a->snap, a->snap,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int j = 0; j + 1 < len; ++j)
+            if (int rc = run_pass_snap(ctx, PASS_STATE, a->seg + (size_t)j * a->snap,
+                                       a->seg + (size_t)(j + 1) * a->snap, nullptr, nullptr,
+                                       nullptr, nullptr))
+                return rc;
+        // reverse through it, reading each state where it lies
         for (int j = len - 1; j >= 0; --j) {
-            if (int rc = restore(ctx, a->seg + (size_t)j * a->snap, t0 + j)) return rc;
-            if (int rc = run_pass(ctx, PASS_MACROS, ctx->stream, phi, p, u, mu)) return rc;
-            CK(adj_d2q9_step(a->real, &ctx->pd, nx, ny, ctx->f[0], ctx->g[0], phi, mu, p, u,
+            const char *sj = a->seg + (size_t)j * a->snap;
+            if (int rc = run_pass_snap(ctx, PASS_MACROS, sj, nullptr, phi, p, u, mu)) return rc;
+            CK(adj_d2q9_step(a->real, &ctx->pd, nx, ny, sj, sj + ctx->fbytes, phi, mu, p, u,
                              a->lf[cb], a->lg[cb], a->lS[cb], a->lf[cb ^ 1], a->lg[cb ^ 1],
                              a->lS[cb ^ 1], a->work, a->dpar, ctx->stream));
             cb ^= 1;
