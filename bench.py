@@ -374,7 +374,9 @@ def run_native(args, rank, world, local_rank):
                        "by lbm_diagnostics (device-to-host read) of both grids, final "
                        "lbm_moments of both grids to host"},
         "accuracy": accuracy,
-        "gpu_launches": args.steps + 4 * len(plan),
+        # one step kernel per step; per chunk and grid the diagnostics pass,
+        # its reduction and (FP32) the equilibrium-shift update
+        "gpu_launches": args.steps + len(plan) * len(cases) * (3 if prec == "fp32" else 2),
         "clocks": clk.summary(t_start, t_end),
         "wall_s_timed_region": t_wall,
     }
@@ -526,7 +528,10 @@ def run_coalescence3d(args, rank, world, local_rank):
         "mass_drift_rel": (d_last["sum_phi"] - d_first["sum_phi"]) / d_first["sum_phi"],
         "u_max_final": d_last["u_max"],
         "clocks": clk.summary(t_start, t_end),
-        "gpu_launches": 2 * args.steps + 2 * len(plan),
+        # two passes per step; per chunk the diagnostics (both passes and the
+        # reduction) plus the FP32 shift update or the offset-scale refresh
+        "gpu_launches": 2 * args.steps + len(plan) * (
+            4 if args.precision == "fp32" else (6 if "off" in args.precision else 3)),
     }), flush=True)
 
 
