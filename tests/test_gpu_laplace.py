@@ -6,9 +6,9 @@ sigma = 1e-3, M = 0.05, nu_l/nu_v = 10, density ratios 10 and 100) after
   the droplet's centre and the far corner equals sigma / R within a few per
   cent (R from the droplet's area).  After 50 000 steps the chemical
   potential of this large droplet is not yet uniform (it relaxes by
-  diffusion, M = 0.05, over R = 128), so part of the jump is still carried by
-  the hydrodynamic p; the total already matches (measured on GB300: the
-  hydrodynamic p then still spans about sigma / R);
+  diffusion, M = 0.05, over R = 128), so the jump is still carried by the
+  hydrodynamic p rather than by phi mu (measured on GB300: p spans about
+  sigma / R); the total already matches;
 * FP32 against FP64 after the same steps: phi within 1e-5 and the spurious
   velocity at or below 1e-6 (the FP32 targets)."""
 import numpy as np
