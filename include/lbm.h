@@ -152,6 +152,26 @@ int lbm_params_default(lbm_params *out);
 int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params,
                void *cuda_stream, lbm_ctx **out);
 
+/* Byte sizes of the device state of a problem: out[0] one f buffer, out[1]
+ * one g buffer, out[2] S_prev (the state is double-buffered: two f and two g
+ * buffers).  For callers that supply the state memory themselves
+ * (lbm_create_with_buffers).  Errors: INVALID_ARG (NULL out, or a problem
+ * lbm_create rejects); no CUDA call is made. */
+int lbm_state_bytes(const lbm_grid *grid, int lattice, const lbm_params *params, size_t out[3]);
+
+/* As lbm_create, but the state lives in memory the caller owns -- for example
+ * device tensors of a framework that manages its own pool, so that the
+ * framework accounts for the populations, which are nearly all of the
+ * footprint.  buffers = {f buffer 0, f buffer 1, g buffer 0, g buffer 1,
+ * S_prev}, device pointers on the current device of at least the sizes
+ * lbm_state_bytes reports (out[0] for the f buffers, out[1] for g, out[2]
+ * for S_prev), each 256-byte aligned.  They are used in place, never freed
+ * by the library, and must stay valid until lbm_destroy; lbm_save's payload
+ * is their contents.  The small work buffers are still allocated here.
+ * Errors: as lbm_create, and INVALID_ARG for a NULL or misaligned buffer. */
+int lbm_create_with_buffers(const lbm_grid *grid, int lattice, const lbm_params *params,
+                            void *cuda_stream, void *const buffers[5], lbm_ctx **out);
+
 /* Set the initial condition from an order-parameter field phi[N] (FP64):
  * f = f^eq(phi, mu(phi)) (Eq. H_i), g = 0 (p = 0, u = 0), S_prev = 0, time 0.
  * on_device = 0: host array (copied, the call returns once it is read);

@@ -32,7 +32,8 @@ EXPORTS = ("lbm_params_default", "lbm_create", "lbm_init_phi", "lbm_step", "lbm_
            "lbm_destroy", "lbm_strerror", "lbm_diagnostics_noalloc", "lbm_batch_create",
            "lbm_batch_case", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_shape",
            "lbm_batch_destroy", "lbm_batch_set_shape", "lbm_adjoint_create", "lbm_adjoint_forward",
-           "lbm_adjoint_backward", "lbm_adjoint_destroy")
+           "lbm_adjoint_backward", "lbm_adjoint_destroy", "lbm_state_bytes",
+           "lbm_create_with_buffers")
 
 
 class lbm_grid(ctypes.Structure):
@@ -82,6 +83,11 @@ def lib(path: str | None = None):
     L.lbm_params_default.argtypes = [ctypes.POINTER(lbm_params)]
     L.lbm_create.argtypes = [ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_params),
                              vp, ctypes.POINTER(vp)]
+    L.lbm_state_bytes.argtypes = [ctypes.POINTER(lbm_grid), ctypes.c_int,
+                                  ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm_create_with_buffers.argtypes = [ctypes.POINTER(lbm_grid), ctypes.c_int,
+                                          ctypes.POINTER(lbm_params), vp,
+                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(vp)]
     L.lbm_init_phi.argtypes = [vp, dp, ctypes.c_int]
     L.lbm_step.argtypes = [vp, ctypes.c_int]
     L.lbm_moments.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
@@ -163,6 +169,30 @@ def lbm_create(grid, lattice, params, cuda_stream=0):
     h = vp()
     rc = lib().lbm_create(ctypes.byref(grid), int(lattice), ctypes.byref(params),
                           vp(cuda_stream or None), ctypes.byref(h))
+    return rc, h
+
+
+def _grid(grid):
+    if isinstance(grid, lbm_grid):
+        return grid
+    return lbm_grid(*(tuple(grid) + (1,) * (3 - len(grid))))
+
+
+def lbm_state_bytes(grid, lattice, params):
+    """Returns (rc, (f_bytes, g_bytes, S_bytes))."""
+    out = (ctypes.c_size_t * 3)()
+    rc = lib().lbm_state_bytes(ctypes.byref(_grid(grid)), int(lattice), ctypes.byref(params), out)
+    return rc, tuple(int(v) for v in out)
+
+
+def lbm_create_with_buffers(grid, lattice, params, buffers, cuda_stream=0):
+    """Returns (rc, handle); ``buffers`` = five device tensors (or raw device
+    addresses): f buffer 0, f buffer 1, g buffer 0, g buffer 1, S_prev."""
+    arr = (ctypes.c_void_p * 5)(*[addr(b) if not isinstance(b, int) else b for b in buffers])
+    h = vp()
+    rc = lib().lbm_create_with_buffers(ctypes.byref(_grid(grid)), int(lattice),
+                                       ctypes.byref(params), vp(cuda_stream or None), arr,
+                                       ctypes.byref(h))
     return rc, h
 
 

@@ -43,6 +43,7 @@ struct lbm_ctx {
     size_t fbytes, gbytes;  // bytes of one f / g state buffer
     float *scw;  // offset storage: target scales [2], then 2 words of scratch
     float *eqs;  // FP32 equilibrium shift {buffer 0, buffer 1, target} (device)
+    int own_state;  // f[], g[] and S were allocated here (not by the caller)
     int recentre;  // lbm_diagnostics moves the FP32 equilibrium shift (not under an adjoint)
     int nsm;
     void *f[2], *g[2], *S;
@@ -311,8 +312,12 @@ void fill_diag(const DiagPartial &r, long long step, lbm_diag *out)
 void free_all(lbm_ctx *c)
 {
     if (c->gexec_valid) cudaGraphExecDestroy(c->gexec);
-    void *dev[] = {c->f[0], c->f[1], c->g[0],     c->g[1], c->S,   c->aux,
-                   c->phiw, c->stage, c->partials, c->dres, c->scw, c->eqs};
+    if (c->own_state) {
+        void *st[] = {c->f[0], c->f[1], c->g[0], c->g[1], c->S};
+        for (void *p : st)
+            if (p) cudaFree(p);
+    }
+    void *dev[] = {c->aux, c->phiw, c->stage, c->partials, c->dres, c->scw, c->eqs};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->hres) cudaFreeHost(c->hres);
@@ -344,8 +349,69 @@ int lbm_params_default(lbm_params *out)
     return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// bytes of one f buffer, one g buffer and S_prev of a valid problem
+void state_sizes(const lbm_grid *grid, int lattice, const lbm_params *params, size_t *fb,
+                 size_t *gb, size_t *sb)
+{
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    const int Q = lattice == LBM_D3Q19 ? 19 : 9, D = lattice == LBM_D3Q19 ? 3 : 2;
+    if (params->precision == LBM_FP32_F16OFF || params->precision == LBM_FP32_BF16OFF) {
+        const OffsetLayout L = offset_layout(N, Q, D);
+        *fb = L.fbytes;
+        *gb = L.gbytes;
+        *sb = (size_t)N * 4;
+        return;
+    }
+    const size_t esz = params->precision == LBM_FP64 ? 8 : 4;
+    const int nf = Q + (params->precision == LBM_FP32 ? 1 : 0);
+    *fb = (size_t)nf * N * esz;
+    *gb = (size_t)Q * N * esz;
+    *sb = (size_t)N * esz;
+}
+
+int create_impl(const lbm_grid *grid, int lattice, const lbm_params *params, void *cuda_stream,
+                void *const *bufs, lbm_ctx **out);
+
+}  // namespace
+
+extern "C" {
+
 int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void *cuda_stream,
                lbm_ctx **out)
+{
+    return create_impl(grid, lattice, params, cuda_stream, nullptr, out);
+}
+
+int lbm_state_bytes(const lbm_grid *grid, int lattice, const lbm_params *params, size_t out[3])
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    int rc = validate(grid, lattice, params);
+    if (rc != LBM_OK) return rc;
+    state_sizes(grid, lattice, params, &out[0], &out[1], &out[2]);
+    return LBM_OK;
+}
+
+int lbm_create_with_buffers(const lbm_grid *grid, int lattice, const lbm_params *params,
+                            void *cuda_stream, void *const buffers[5], lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!buffers) return LBM_ERR_INVALID_ARG;
+    for (int k = 0; k < 5; ++k)
+        if (!buffers[k] || ((uintptr_t)buffers[k] & 255u)) return LBM_ERR_INVALID_ARG;
+    return create_impl(grid, lattice, params, cuda_stream, buffers, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_impl(const lbm_grid *grid, int lattice, const lbm_params *params, void *cuda_stream,
+                void *const *bufs, lbm_ctx **out)
 {
     if (!out) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
@@ -419,11 +485,21 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
         }
     };
     (void)Q;
-    dalloc(&ctx->f[0], ctx->fbytes);
-    dalloc(&ctx->f[1], ctx->fbytes);
-    dalloc(&ctx->g[0], ctx->gbytes);
-    dalloc(&ctx->g[1], ctx->gbytes);
-    dalloc(&ctx->S, N * ssz);
+    if (bufs) {  // the caller's memory, used in place
+        ctx->f[0] = bufs[0];
+        ctx->f[1] = bufs[1];
+        ctx->g[0] = bufs[2];
+        ctx->g[1] = bufs[3];
+        ctx->S = bufs[4];
+        ctx->own_state = 0;
+    } else {
+        ctx->own_state = 1;
+        dalloc(&ctx->f[0], ctx->fbytes);
+        dalloc(&ctx->f[1], ctx->fbytes);
+        dalloc(&ctx->g[0], ctx->gbytes);
+        dalloc(&ctx->g[1], ctx->gbytes);
+        dalloc(&ctx->S, N * ssz);
+    }
     dalloc((void **)&ctx->aux, N * sizeof(double));
     if (lattice == LBM_D3Q19) dalloc(&ctx->phiw, N * ssz);
     if (ctx->codec >= 0) dalloc((void **)&ctx->scw, 4 * sizeof(float));
@@ -453,6 +529,10 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, void
     *out = ctx;
     return LBM_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
 {

@@ -66,6 +66,29 @@ def test_offset_storage_needs_d3q19(capi):
         assert capi.lbm_create((16, 16), capi.LBM_D2Q9, p)[0] == capi.LBM_ERR_INVALID_ARG
 
 
+def test_state_bytes_and_caller_buffers(capi):
+    """lbm_state_bytes reports the double-buffered state's sizes without a GPU;
+    lbm_create_with_buffers refuses missing or misaligned buffers first."""
+    p = capi.lbm_params_default()                      # FP32: rest population pair
+    rc, (fb, gb, sb) = capi.lbm_state_bytes((30, 20), capi.LBM_D2Q9, p)
+    assert rc == 0 and (fb, gb, sb) == (10 * 600 * 4, 9 * 600 * 4, 600 * 4)
+    p.precision = capi.LBM_FP64
+    rc, sizes = capi.lbm_state_bytes((30, 20, 7), capi.LBM_D3Q19, p)
+    assert rc == 0 and sizes == (19 * 4200 * 8, 19 * 4200 * 8, 4200 * 8)
+    p.precision = capi.LBM_FP32_F16OFF                 # 16-bit offsets, 7 FP32 fields, scales
+    rc, (fb, gb, sb) = capi.lbm_state_bytes((30, 20, 7), capi.LBM_D3Q19, p)
+    pad = lambda b: (b + 255) // 256 * 256
+    assert rc == 0 and fb == pad(19 * 4200 * 2) + pad(7 * 4200 * 4) + 256
+    assert gb == 19 * 4200 * 2 and sb == 4200 * 4
+    p.W = 0.0
+    assert capi.lbm_state_bytes((30, 20), capi.LBM_D2Q9, p)[0] == capi.LBM_ERR_INVALID_ARG
+    p = capi.lbm_params_default()
+    rc, h = capi.lbm_create_with_buffers((16, 16), capi.LBM_D2Q9, p, [0] * 5)
+    assert rc == capi.LBM_ERR_INVALID_ARG and not h.value
+    rc, h = capi.lbm_create_with_buffers((16, 16), capi.LBM_D2Q9, p, [4096 + 8] * 5)
+    assert rc == capi.LBM_ERR_INVALID_ARG and not h.value
+
+
 def test_null_safety_and_strerror(capi):
     L = capi.lib()
     L.lbm_destroy(None)

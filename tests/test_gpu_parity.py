@@ -205,6 +205,40 @@ def test_fp32_equilibrium_shift_is_exact(gpu, lattice, shape):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("lattice,shape,precision", [("D2Q9", (144, 50), "fp32"),
+                                                    ("D2Q9", (144, 50), "fp64"),
+                                                    ("D3Q19", (36, 20, 12), "f16off")])
+def test_create_with_caller_buffers(gpu, lattice, shape, precision):
+    """A context on caller-owned device memory (torch tensors) steps exactly
+    like one that allocates its own state, and leaves the memory to its owner."""
+    torch = pytest.importorskip("torch")
+    from paper_2311_10827_gb300 import capi, sim
+    prm = dict(PRM, W=5.0) if lattice == "D3Q19" else PRM
+    params = sim.make_params(precision, **prm)
+    lat = capi.LBM_D3Q19 if lattice == "D3Q19" else capi.LBM_D2Q9
+    rc, (fb, gb, sb) = capi.lbm_state_bytes(shape, lat, params)
+    assert rc == 0
+    bufs = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in (fb, fb, gb, gb, sb)]
+    rc, h = capi.lbm_create_with_buffers(shape, lat, params, bufs)
+    assert rc == 0
+    a = sim.Simulation(shape, lattice=lattice, precision=precision, _borrow=h, **prm)
+    b = sim.Simulation(shape, lattice=lattice, precision=precision, **prm)
+    nx, ny = shape[0], shape[1]
+    nz = shape[2] if len(shape) > 2 else 1
+    phi0 = wl.droplet(nx, ny, 8.0, prm["W"], nz=nz)
+    for s in (a, b):
+        s.init_phi(phi0)
+        s.step(45)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    capi.lbm_destroy(h)
+    torch.cuda.synchronize()
+    for t in bufs:            # still the caller's, still usable
+        t.zero_()
+    torch.cuda.synchronize()
+    assert int(bufs[0].sum()) == 0
+
+
 def test_fused_diagnostics_equal_on_demand(gpu):
     a = gpu.Simulation((130, 60), precision="fp64", diag_every=10, **PRM)
     b = gpu.Simulation((130, 60), precision="fp64", **PRM)
