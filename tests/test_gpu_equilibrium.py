@@ -55,6 +55,15 @@ def runs():
                    "fp32": (s32.diagnostics(), s32.moments())}
 
 
+def div_h(u):
+    """(1/3) axis differences + (1/12) diagonal differences on the periodic grid."""
+    def d(a, axis):
+        o = 1 - axis
+        c = np.roll(a, -1, axis) - np.roll(a, 1, axis)
+        return c / 3 + (np.roll(c, -1, o) + np.roll(c, 1, o)) / 12
+    return d(u[0], 1) + d(u[1], 0)
+
+
 def test_fp64_droplet_reaches_paper_magnitudes(runs):
     steps, r = runs
     d, m = r["fp64"]
@@ -62,6 +71,8 @@ def test_fp64_droplet_reaches_paper_magnitudes(runs):
     assert d["kinetic_energy"] < E_TARGET, (steps, d["kinetic_energy"])
     assert d["mu_max"] - d["mu_min"] < 1e-11
     assert not d["nonfinite"]
+    # divergence-free velocity (isotropic D2Q9 gradient of Eq. gradient)
+    assert np.abs(div_h(m["u"])).max() < 1e-14
     # the droplet keeps its tanh profile (bulk values within 1e-2 of phi_l, phi_v)
     assert abs(m["phi"].max() - 1.0) < 1e-2 and abs(m["phi"].min()) < 1e-2
 
