@@ -336,7 +336,8 @@ typedef struct lbm_adjoint lbm_adjoint;
 
 /* Attach an adjoint recorder to ctx (D2Q9) for runs of at most max_steps
  * steps; allocates max_steps / checkpoint_every + 1 checkpoints and one
- * segment of checkpoint_every states.  Errors: INVALID_ARG (D3Q19 context,
+ * segment of checkpoint_every states, each with its moments (phi, mu, p, u:
+ * 5 values per node).  Errors: INVALID_ARG (D3Q19 context,
  * checkpoint_every < 1, max_steps < 1), OOM, CUDA. */
 int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_adjoint **out);
 

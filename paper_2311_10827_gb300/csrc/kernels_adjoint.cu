@@ -2,15 +2,20 @@
 // loss on the final order parameter with respect to the initial field phi0,
 // the surface tension (through kappa and beta) and the mobility (through
 // 1/tau_f).  Not in the paper: the derivative of the discrete map, stage by
-// stage in reverse order.  Adjoint arithmetic and adjoint fields are in the
-// context's precision (FP64, or FP32 for the FP32 form; the parameter
-// gradients accumulate in FP64); the forward state is read at its own
-// precision.  Adjoint fields use the paper's convention
-// (pre-collision populations f_i(x, t), [Q][N]).
+// stage in reverse order.  Adjoint arithmetic, adjoint fields, the forward
+// moments and the parameters are all in the context's precision R (FP64, or
+// FP32 for the FP32 form: FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this GPU, so the FP32 adjoint does none per node); only the
+// per-block sums of the parameter gradients are accumulated in FP64.
+// Adjoint fields use the paper's convention
+// (pre-collision populations f_i(x, t), [Q][N]).  The adjoint of f is kept
+// as lf[i] + lpt: the adjoint of phi = sum_i f_i adds the same value to every
+// direction of a node, so it is stored once per node (lpt) instead of being
+// added into all Q arrays.
 //
 // One reverse step (state at time n, adjoint of the state at n + 1):
 //   1. the forward moments of time n (phi, mu, p, u) come from the ordinary
-//      moments pass (FP64 fields);
+//      moments pass (fields in the storage type);
 //   2. adj_local: reverse streaming, then per node the reverse of both
 //      collisions and of the moments, leaving the adjoint of g and S_prev,
 //      the direct part of the adjoint of f, and the local adjoints of phi,
@@ -39,11 +44,9 @@ __host__ __device__ constexpr double wa(int i) { return i == 0 ? 4.0 / 9.0 : (i 
 __host__ __device__ constexpr double ba(int i) { return i == 0 ? -2.0 : (i <= 4 ? -0.5 : 1.0); }
 constexpr double CS2A = 1.0 / 3.0;
 
-__device__ __forceinline__ int wrapa(int c, int n)
-{
-    int r = c % n;
-    return r < 0 ? r + n : r;
-}
+// periodic wrap of a neighbour coordinate c in [-1, n] (every stencil here
+// reaches one node at most)
+__device__ __forceinline__ int wrapa(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
 struct AdjGeom {
     int nx, ny;
@@ -55,46 +58,49 @@ __device__ __forceinline__ unsigned at(const AdjGeom &g, int x, int y, int dx, i
     return (unsigned)wrapa(y + dy, g.ny) * g.nx + wrapa(x + dx, g.nx);
 }
 
-// isotropic gradient of an FP64 field at (x, y): (1/cs2) sum w_i c_i psi(x + c_i)
+// isotropic gradient of a field at (x, y): (1/cs2) sum w_i c_i psi(x + c_i)
 template <typename R>
-__device__ __forceinline__ void grad_at(const AdjGeom &g, const double *psi, int x, int y, R &gx,
+__device__ __forceinline__ void grad_at(const AdjGeom &g, const R *psi, int x, int y, R &gx,
                                         R &gy)
 {
     gx = R(0), gy = R(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const R v = (R)psi[at(g, x, y, cxa(i), cya(i))];
+        const R v = psi[at(g, x, y, cxa(i), cya(i))];
         gx += R(wa(i) * cxa(i) / CS2A) * v;
         gy += R(wa(i) * cya(i) / CS2A) * v;
     }
 }
 
-// one FP64 atomic per block for a per-thread partial (warp shuffles, then
-// the warps' sums in shared memory); every thread of the block calls it
-__device__ __forceinline__ void block_add(double v, double *dst)
+// one FP64 atomic per block for a per-thread partial: the block's sum is
+// formed in R (warp shuffles, then the warps' sums through shared memory) and
+// converted once; every thread of the block calls it
+template <typename R>
+__device__ __forceinline__ void block_add(R v, double *dst)
 {
-    __shared__ double part[32];
+    __shared__ R part[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();  // part[] may still be read by an earlier call
     if (lane == 0) part[wid] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
+        R s = R(0);
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        if (s != 0.0) atomicAdd(dst, s);
+        if (s != R(0)) atomicAdd(dst, (double)s);
     }
 }
 
 // lambda_phi, lambda_mu, lambda_grad phi, lambda_grad mu and dL/d(1/tau_f);
 // the FP32 form fits 80 registers (3 resident CTAs per SM instead of 2: the
 // kernel waits on gathered loads, so more warps help)
-template <typename T, typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) adj_local(const StepParams<double> P, AdjGeom geo, const T *__restrict__ f,
-                          const T *__restrict__ g, int rest_pair, const double *__restrict__ phi,
-                          const double *__restrict__ mu, const double *__restrict__ pf,
-                          const double *__restrict__ uf, const R *__restrict__ lf_in,
-                          const R *__restrict__ lg_in, const R *__restrict__ lS_in,
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
+    adj_local(const StepParams<R> P, AdjGeom geo, const R *__restrict__ f,
+              const R *__restrict__ g, const R *__restrict__ phi, const R *__restrict__ mu,
+              const R *__restrict__ pf, const R *__restrict__ uf, const R *__restrict__ lf_in,
+                          const R *__restrict__ lpt_in, const R *__restrict__ lg_in,
+                          const R *__restrict__ lS_in,
                           R *__restrict__ lf_out, R *__restrict__ lg_out, R *__restrict__ lS_out,
                           R *__restrict__ lphi, R *__restrict__ lmu, R *__restrict__ lgphi,
                           R *__restrict__ lgmu, double *dpar)
@@ -105,17 +111,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) adj_local(const S
     R itf_part = R(0);
     if (n < N) {
         const int x = n % geo.nx, y = n / geo.nx;
-        const R ph = (R)phi[n], m = (R)mu[n], p = (R)pf[n];
-        const R u[2] = {(R)uf[n], (R)uf[N + n]};
+        const R ph = phi[n], m = mu[n], p = pf[n];
+        const R u[2] = {uf[n], uf[N + n]};
         R gph[2], gmu[2];
         grad_at(geo, phi, x, y, gph[0], gph[1]);
         grad_at(geo, mu, x, y, gmu[0], gmu[1]);
-        const R drho = (R)P.drho, dnu = (R)P.dnu;
-        const R rho = (R)P.rhov + (ph - (R)P.phiv) * drho;
-        const R nu = (R)P.nuv + (ph - (R)P.phiv) * dnu;
+        const R drho = P.drho, dnu = P.dnu;
+        const R rho = P.rhov + (ph - P.phiv) * drho;
+        const R nu = P.nuv + (ph - P.phiv) * dnu;
         const R itg = R(1) / (R(0.5) + nu * IC);
-        const R itf = (R)P.inv_tauf, alpha = (R)P.alpha;
-        const R F[2] = {-ph * gmu[0] + (R)P.G[0], -ph * gmu[1] + (R)P.G[1]};
+        const R itf = P.inv_tauf, alpha = P.alpha;
+        const R F[2] = {-ph * gmu[0] + P.G[0], -ph * gmu[1] + P.G[1]};
         const R gr[2] = {drho * gph[0], drho * gph[1]};
         const R ugr = u[0] * gr[0] + u[1] * gr[1], uu = u[0] * u[0] + u[1] * u[1];
 
@@ -124,10 +130,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) adj_local(const S
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const unsigned src = at(geo, x, y, -cxa(i), -cya(i));
-            fv[i] = (R)f[i * N + src];
-            gv[i] = (R)g[i * N + src];
+            fv[i] = f[i * N + src];
+            gv[i] = g[i * N + src];
         }
-        if (rest_pair) fv[0] += (R)f[9 * N + n];
+        if (sizeof(R) == 4) fv[0] += f[9 * N + n];  // FP32: the rest population's low word
 
         R lu[2] = {0, 0}, lF[2] = {0, 0}, lgr[2] = {0, 0}, lgp[2] = {0, 0};
         R lrho = 0, lp = 0, lSx = 0, litg = 0, lph = 0, lmux = 0, lsrc = 0;
@@ -135,7 +141,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) adj_local(const S
         // CH collision: f* = (1 - 1/tau_f) f + f^eq/tau_f + w_i b_i (1.5 S - 0.5 S_prev)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const R l = lf_in[i * N + at(geo, x, y, cxa(i), cya(i))];  // reverse streaming
+            const unsigned src = at(geo, x, y, cxa(i), cya(i));  // reverse streaming
+            const R l = lf_in[i * N + src] + lpt_in[src];
             const R fe = i == 0 ? ph - R(1.0 - wa(0)) * alpha * m : R(wa(i)) * alpha * m;
             lf_out[i * N + n] = (R(1) - itf) * l;
             itf_part += l * (fe - fv[i]);
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) adj_local(const S
         lmu[n] = lmux;
     }
     // dL/d(1/tau_f): one FP64 atomic per block
-    block_add((double)itf_part, dpar + 2);
+    block_add(itf_part, dpar + 2);
 }
 
 // transpose of the gradient stencil: (G^T v)(y) = (1/cs2) sum_i w_i c_i . v(y - c_i)
@@ -261,11 +268,12 @@ __global__ void adj_mu(AdjGeom geo, const R *__restrict__ lmu, const R *__restri
     lmu_tot[n] = lmu[n] + gradT_at(geo, lgmu, x, y);
 }
 
-// lambda_phi total; lambda_f += lambda_phi for every i; dL/dkappa, dL/dbeta
-template <typename R>
-__global__ void adj_phi(const StepParams<double> P, AdjGeom geo, const double *__restrict__ phi,
+// lambda_phi total (the part of lambda_f common to every direction, lpt_out);
+// dL/dkappa, dL/dbeta
+template <typename R, typename V>
+__global__ void adj_phi(const StepParams<R> P, AdjGeom geo, const V *__restrict__ phi,
                         const R *__restrict__ lphi, const R *__restrict__ lgphi,
-                        const R *__restrict__ lmu_tot, R *__restrict__ lf_out, double *lphi_out,
+                        const R *__restrict__ lmu_tot, R *__restrict__ lpt_out, double *lphi_out,
                         double *dpar)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,130 +281,138 @@ __global__ void adj_phi(const StepParams<double> P, AdjGeom geo, const double *_
     if (n < geo.N) {
         const int x = n % geo.nx, y = n / geo.nx;
         const R ph = (R)phi[n], lm = lmu_tot[n];
-        const R a = ph - (R)P.phil, b = ph - (R)P.phiv, c = ph - (R)P.phibar;
-        const R d2psi = R(4) * (R)P.beta * (b * c + a * c + a * b);
+        const R a = ph - P.phil, b = ph - P.phiv, c = ph - P.phibar;
+        const R d2psi = R(4) * P.beta * (b * c + a * c + a * b);
         const R l = lphi[n] + gradT_at(geo, lgphi, x, y) + d2psi * lm -
-                    (R)P.kappa * lap_at<R>(geo, lmu_tot, x, y);
+                    P.kappa * lap_at<R>(geo, lmu_tot, x, y);
         dk = lm * (-lap_at<R>(geo, phi, x, y));
         db = lm * R(4) * a * b * c;
-        if (lf_out) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) lf_out[i * geo.N + n] += l;
-        }
+        if (lpt_out) lpt_out[n] = l;
         if (lphi_out) lphi_out[n] = (double)l;
     }
-    block_add((double)dk, dpar + 0);
-    block_add((double)db, dpar + 1);
+    block_add(dk, dpar + 0);
+    block_add(db, dpar + 1);
 }
 
 // initial condition f = f^eq(phi0, mu(phi0)): lambda_phi and lambda_mu from lambda_f
 template <typename R>
-__global__ void adj_init_local(const StepParams<double> P, AdjGeom geo, const R *__restrict__ lf,
-                               R *__restrict__ lphi, R *__restrict__ lmu, R *__restrict__ lgphi)
+__global__ void adj_init_local(const StepParams<R> P, AdjGeom geo, const R *__restrict__ lf,
+                               const R *__restrict__ lpt, R *__restrict__ lphi,
+                               R *__restrict__ lmu, R *__restrict__ lgphi)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= geo.N) return;
-    const R alpha = (R)P.alpha;
-    R l = -R(1.0 - wa(0)) * alpha * lf[n];
+    const R alpha = P.alpha, lp = lpt[n];
+    R l = -R(1.0 - wa(0)) * alpha * (lf[n] + lp);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) l += R(wa(i)) * alpha * lf[i * geo.N + n];
+    for (int i = 1; i < 9; ++i) l += R(wa(i)) * alpha * (lf[i * geo.N + n] + lp);
     lmu[n] = l;
-    lphi[n] = lf[n];
+    lphi[n] = lf[n] + lp;
     lgphi[n] = R(0);
     lgphi[geo.N + n] = R(0);
 }
 
 // adjoint of the final state for L(phi^N): lambda_f_i = dL/dphi for every i
+// (all of it in the common part lpt)
 template <typename R>
 __global__ void adj_seed(unsigned N, const double *__restrict__ dphi, R *__restrict__ lf,
-                         R *__restrict__ lg, R *__restrict__ lS)
+                         R *__restrict__ lpt, R *__restrict__ lg, R *__restrict__ lS)
 {
     const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const R v = (R)dphi[n];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        lf[i * N + n] = v;
+        lf[i * N + n] = R(0);
         lg[i * N + n] = R(0);
     }
+    lpt[n] = (R)dphi[n];
     lS[n] = R(0);
 }
 
 template <typename R>
-void adj_step_t(int precision, const StepParams<double> &P, AdjGeom geo, const void *f,
-                const void *g, const double *phi, const double *mu, const double *p,
-                const double *u, const R *lf_in, const R *lg_in, const R *lS_in, R *lf_out,
-                R *lg_out, R *lS_out, R *work, double *dpar, cudaStream_t st)
+void adj_step_t(const StepParams<R> &P, AdjGeom geo, const R *f, const R *g, const R *phi,
+                const R *mu, const R *p, const R *u, const R *lf_in, R *lpt, const R *lg_in,
+                const R *lS_in, R *lf_out, R *lg_out, R *lS_out, R *work, double *dpar,
+                cudaStream_t st)
 {
     const unsigned N = geo.N;
     R *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N, *lgmu = work + 4 * (size_t)N,
       *lmu_tot = work + 6 * (size_t)N;
     const unsigned nb = (N + 255) / 256;
-    if (precision == 0)
-        adj_local<double, R><<<nb, 256, 0, st>>>(P, geo, (const double *)f, (const double *)g, 0,
-                                                 phi, mu, p, u, lf_in, lg_in, lS_in, lf_out,
-                                                 lg_out, lS_out, lphi, lmu, lgphi, lgmu, dpar);
-    else
-        adj_local<float, R><<<nb, 256, 0, st>>>(P, geo, (const float *)f, (const float *)g, 1, phi,
-                                                mu, p, u, lf_in, lg_in, lS_in, lf_out, lg_out,
-                                                lS_out, lphi, lmu, lgphi, lgmu, dpar);
+    adj_local<R><<<nb, 256, 0, st>>>(P, geo, f, g, phi, mu, p, u, lf_in, lpt, lg_in, lS_in,
+                                     lf_out, lg_out, lS_out, lphi, lmu, lgphi, lgmu, dpar);
     adj_mu<R><<<nb, 256, 0, st>>>(geo, lmu, lgmu, lmu_tot);
-    adj_phi<R><<<nb, 256, 0, st>>>(P, geo, phi, lphi, lgphi, lmu_tot, lf_out, nullptr, dpar);
+    // lpt is read (gathered) by adj_local above and rewritten here
+    adj_phi<R, R><<<nb, 256, 0, st>>>(P, geo, phi, lphi, lgphi, lmu_tot, lpt, nullptr, dpar);
 }
 
 template <typename R>
-void adj_init_t(const StepParams<double> &P, AdjGeom geo, const double *phi0, const R *lf,
-                R *work, double *lphi0, double *dpar, cudaStream_t st)
+void adj_init_t(const StepParams<R> &P, AdjGeom geo, const double *phi0, const R *lf,
+                const R *lpt, R *work, double *lphi0, double *dpar, cudaStream_t st)
 {
     const unsigned N = geo.N;
     R *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N;
     const unsigned nb = (N + 255) / 256;
-    adj_init_local<R><<<nb, 256, 0, st>>>(P, geo, lf, lphi, lmu, lgphi);
-    adj_phi<R><<<nb, 256, 0, st>>>(P, geo, phi0, lphi, lgphi, lmu, nullptr, lphi0, dpar);
+    adj_init_local<R><<<nb, 256, 0, st>>>(P, geo, lf, lpt, lphi, lmu, lgphi);
+    adj_phi<R, double><<<nb, 256, 0, st>>>(P, geo, phi0, lphi, lgphi, lmu, nullptr, lphi0, dpar);
+}
+
+template <typename R>
+void adj_step_r(const void *params, AdjGeom geo, const void *f, const void *g, const void *mom,
+                const void *lf_in, void *lpt, const void *lg_in, const void *lS_in, void *lf_out,
+                void *lg_out, void *lS_out, void *work, double *dpar, cudaStream_t st)
+{
+    const R *m = static_cast<const R *>(mom);
+    const size_t N = geo.N;
+    adj_step_t<R>(*static_cast<const StepParams<R> *>(params), geo, static_cast<const R *>(f),
+                  static_cast<const R *>(g), m, m + N, m + 2 * N, m + 3 * N,
+                  static_cast<const R *>(lf_in), static_cast<R *>(lpt),
+                  static_cast<const R *>(lg_in), static_cast<const R *>(lS_in),
+                  static_cast<R *>(lf_out), static_cast<R *>(lg_out), static_cast<R *>(lS_out),
+                  static_cast<R *>(work), dpar, st);
 }
 
 }  // namespace
 
-cudaError_t adj_d2q9_seed(int real, int N, const double *dphi, void *lf, void *lg, void *lS,
-                          cudaStream_t st)
+cudaError_t adj_d2q9_seed(int real, int N, const double *dphi, void *lf, void *lpt, void *lg,
+                          void *lS, cudaStream_t st)
 {
     if (real == 0)
         adj_seed<double><<<(N + 255) / 256, 256, 0, st>>>((unsigned)N, dphi, (double *)lf,
-                                                          (double *)lg, (double *)lS);
+                                                          (double *)lpt, (double *)lg, (double *)lS);
     else
         adj_seed<float><<<(N + 255) / 256, 256, 0, st>>>((unsigned)N, dphi, (float *)lf,
-                                                         (float *)lg, (float *)lS);
+                                                         (float *)lpt, (float *)lg, (float *)lS);
     return cudaGetLastError();
 }
 
-cudaError_t adj_d2q9_step(int precision, const void *params64, int nx, int ny, const void *f,
-                          const void *g, const double *phi, const double *mu, const double *p,
-                          const double *u, const void *lf_in, const void *lg_in, const void *lS_in,
-                          void *lf_out, void *lg_out, void *lS_out, void *work, double *dpar,
-                          cudaStream_t st)
+cudaError_t adj_d2q9_step(int real, const void *params, int nx, int ny, const void *f,
+                          const void *g, const void *moments, const void *lf_in, void *lpt,
+                          const void *lg_in, const void *lS_in, void *lf_out, void *lg_out,
+                          void *lS_out, void *work, double *dpar, cudaStream_t st)
 {
-    const StepParams<double> &P = *static_cast<const StepParams<double> *>(params64);
-    const AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
-    if (precision == 0)
-        adj_step_t<double>(0, P, geo, f, g, phi, mu, p, u, (const double *)lf_in,
-                           (const double *)lg_in, (const double *)lS_in, (double *)lf_out,
-                           (double *)lg_out, (double *)lS_out, (double *)work, dpar, st);
-    else
-        adj_step_t<float>(1, P, geo, f, g, phi, mu, p, u, (const float *)lf_in,
-                          (const float *)lg_in, (const float *)lS_in, (float *)lf_out,
-                          (float *)lg_out, (float *)lS_out, (float *)work, dpar, st);
-    return cudaGetLastError();
-}
-
-cudaError_t adj_d2q9_init(int real, const void *params64, int nx, int ny, const double *phi0,
-                          const void *lf, void *work, double *lphi0, double *dpar, cudaStream_t st)
-{
-    const StepParams<double> &P = *static_cast<const StepParams<double> *>(params64);
     const AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
     if (real == 0)
-        adj_init_t<double>(P, geo, phi0, (const double *)lf, (double *)work, lphi0, dpar, st);
+        adj_step_r<double>(params, geo, f, g, moments, lf_in, lpt, lg_in, lS_in, lf_out, lg_out,
+                           lS_out, work, dpar, st);
     else
-        adj_init_t<float>(P, geo, phi0, (const float *)lf, (float *)work, lphi0, dpar, st);
+        adj_step_r<float>(params, geo, f, g, moments, lf_in, lpt, lg_in, lS_in, lf_out, lg_out,
+                          lS_out, work, dpar, st);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_d2q9_init(int real, const void *params, int nx, int ny, const double *phi0,
+                          const void *lf, const void *lpt, void *work, double *lphi0, double *dpar,
+                          cudaStream_t st)
+{
+    const AdjGeom geo{nx, ny, (unsigned)((size_t)nx * ny)};
+    if (real == 0)
+        adj_init_t<double>(*static_cast<const StepParams<double> *>(params), geo, phi0,
+                           (const double *)lf, (const double *)lpt, (double *)work, lphi0, dpar,
+                           st);
+    else
+        adj_init_t<float>(*static_cast<const StepParams<float> *>(params), geo, phi0,
+                          (const float *)lf, (const float *)lpt, (float *)work, lphi0, dpar, st);
     return cudaGetLastError();
 }
 

@@ -420,6 +420,14 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
                     a.out_u[(size_t)N + n] = (double)uy;
                 }
             }
+            if (PASS & PASS_MACROS_T) {
+                const size_t n = (size_t)nrow + xo;
+                static_cast<T *>(a.mt_phi)[n] = phi;
+                static_cast<T *>(a.mt_p)[n] = p;
+                static_cast<T *>(a.mt_mu)[n] = mu;
+                static_cast<T *>(a.mt_u)[n] = ux;
+                static_cast<T *>(a.mt_u)[(size_t)N + n] = uy;
+            }
             if (PASS & PASS_STATE) {
                 const unsigned n = nrow + xo;
                 T *__restrict__ fd = static_cast<T *>(a.f_dst);
@@ -688,6 +696,9 @@ cudaError_t pass_t(int pass, const void *params, const PassArgs &a, const Launch
     case PASS_MACROS: return launch_pass<T, PASS_MACROS>(params, a, s, st);
     case PASS_DIAG: return launch_pass<T, PASS_DIAG>(params, a, s, st);
     case PASS_MACROS | PASS_DIAG: return launch_pass<T, PASS_MACROS | PASS_DIAG>(params, a, s, st);
+    case PASS_MACROS_T: return launch_pass<T, PASS_MACROS_T>(params, a, s, st);
+    case PASS_STATE | PASS_MACROS_T:
+        return launch_pass<T, PASS_STATE | PASS_MACROS_T>(params, a, s, st);
     default: return cudaErrorInvalidValue;
     }
 }

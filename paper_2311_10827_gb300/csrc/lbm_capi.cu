@@ -197,8 +197,9 @@ int run_pass(lbm_ctx *ctx, int pass, cudaStream_t st, double *o_phi, double *o_p
 // adjoint's layout) instead of the context's buffers; a time step writes the
 // next state into `next` (same layout).  The equilibrium shift stays at the
 // context's (constant while an adjoint recorder is attached).
-int run_pass_snap(lbm_ctx *ctx, int pass, const char *snap, char *next, double *o_phi,
-                  double *o_p, double *o_u, double *o_mu)
+// moments (PASS_MACROS_T, D2Q9): phi, mu, p (N each) and u (2N) in the
+// storage type, back to back from `moments`
+int run_pass_snap(lbm_ctx *ctx, int pass, const char *snap, char *next, void *moments)
 {
     const size_t fb = ctx->fbytes, gb = ctx->gbytes;
     PassArgs a;
@@ -211,10 +212,14 @@ int run_pass_snap(lbm_ctx *ctx, int pass, const char *snap, char *next, double *
         a.g_dst = next + fb;
         a.S_out = next + fb + gb;
     }
-    a.out_phi = o_phi;
-    a.out_p = o_p;
-    a.out_u = o_u;
-    a.out_mu = o_mu;
+    if (moments) {
+        const size_t nb = (size_t)ctx->N * ctx->esz;
+        char *m = static_cast<char *>(moments);
+        a.mt_phi = m;
+        a.mt_mu = m + nb;
+        a.mt_p = m + 2 * nb;
+        a.mt_u = m + 3 * nb;
+    }
     a.partials = ctx->partials;
     a.eqs_src = ctx->eqs + ctx->cur;
     a.eqs_dst = ctx->eqs + (ctx->cur ^ 1);
@@ -1326,13 +1331,15 @@ struct lbm_adjoint {
     lbm_ctx *ctx;
     int K, max_steps, nsteps, recorded;
     size_t snap;        // bytes of one state snapshot (f, g, S at the context's precision)
+    size_t slot;        // bytes of one segment slot: a snapshot, then its moments
     char *ckpt;         // (max_steps / K + 1) snapshots
-    char *seg;          // K snapshots of the segment being reversed
+    char *seg;          // K slots of the segment being reversed
     int real;           // adjoint arithmetic: 0 FP64, 1 FP32 (the context's precision)
     size_t rsz;         // bytes per adjoint value
     double *phi0;       // N
     void *lf[2], *lg[2], *lS[2];  // adjoint fields at the adjoint precision
-    double *macro;      // phi, mu, p (N each), u (2N)
+    void *lpt;                    // the adjoint of f common to all directions [N]
+    double *macro;      // 5N doubles (host-resident dL/dphi0 staging)
     void *work;         // 7N adjoint values (at least N doubles)
     double *dpar;       // 3
 };
@@ -1364,7 +1371,7 @@ int restore(lbm_ctx *ctx, const char *src, long long step)
 void adjoint_free(lbm_adjoint *a)
 {
     void *p[] = {a->ckpt, a->seg, a->phi0, a->lf[0], a->lf[1], a->lg[0], a->lg[1],
-                 a->lS[0], a->lS[1], a->macro, a->work, a->dpar};
+                 a->lS[0], a->lS[1], a->lpt, a->macro, a->work, a->dpar};
     for (void *q : p)
         if (q) cudaFree(q);
     free(a);
@@ -1389,14 +1396,17 @@ int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_ad
     const size_t N = (size_t)ctx->N, Q = (size_t)ctx->Q;
     a->snap = ((size_t)ctx->nf * N + Q * N + N) * ctx->esz;
     a->snap = (a->snap + 255) / 256 * 256;
+    // phi, mu, p and u (5N values) of each segment state sit after its snapshot
+    a->slot = a->snap + (5 * N * ctx->esz + 255) / 256 * 256;
     const size_t nck = (size_t)(max_steps / checkpoint_every + 1);
     a->real = ctx->prm.precision == LBM_FP64 ? 0 : 1;
     a->rsz = a->real == 0 ? sizeof(double) : sizeof(float);
     bool ok = cudaMalloc((void **)&a->ckpt, nck * a->snap) == cudaSuccess &&
-              cudaMalloc((void **)&a->seg, (size_t)checkpoint_every * a->snap) == cudaSuccess &&
+              cudaMalloc((void **)&a->seg, (size_t)checkpoint_every * a->slot) == cudaSuccess &&
               cudaMalloc((void **)&a->phi0, N * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&a->macro, 5 * N * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&a->work, 7 * N * a->rsz) == cudaSuccess &&
+              cudaMalloc(&a->lpt, N * a->rsz) == cudaSuccess &&
               cudaMalloc((void **)&a->dpar, 3 * sizeof(double)) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b)
         ok = cudaMalloc(&a->lf[b], Q * N * a->rsz) == cudaSuccess &&
@@ -1447,36 +1457,38 @@ int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, d
     CK(cudaMemcpyAsync(seed, dL_dphi, N * sizeof(double),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     int cb = 0;
-    CK(adj_d2q9_seed(a->real, (int)N, seed, a->lf[cb], a->lg[cb], a->lS[cb], ctx->stream));
+    CK(adj_d2q9_seed(a->real, (int)N, seed, a->lf[cb], a->lpt, a->lg[cb], a->lS[cb], ctx->stream));
     CK(cudaMemsetAsync(a->dpar, 0, 3 * sizeof(double), ctx->stream));
-    double *phi = a->macro, *mu = a->macro + N, *p = a->macro + 2 * N, *u = a->macro + 3 * N;
     const int nseg = (a->nsteps + a->K - 1) / a->K;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int t0 = sgi * a->K;
         const int len = a->nsteps - t0 < a->K ? a->nsteps - t0 : a->K;
         // recompute the segment forward from its checkpoint, each step writing
-        // straight into the next state slot of the segment
+        // straight into the next state slot of the segment and the moments of
+        // the state it steps from beside that state (the last state's moments
+        // come from a moments-only pass)
         CK(cudaMemcpyAsync(a->seg, a->ckpt + (size_t)sgi * a->snap, a->snap,
                            cudaMemcpyDeviceToDevice, ctx->stream));
-        for (int j = 0; j + 1 < len; ++j)
-            if (int rc = run_pass_snap(ctx, PASS_STATE, a->seg + (size_t)j * a->snap,
-                                       a->seg + (size_t)(j + 1) * a->snap, nullptr, nullptr,
-                                       nullptr, nullptr))
+        for (int j = 0; j < len; ++j) {
+            char *sj = a->seg + (size_t)j * a->slot;
+            const bool last = j + 1 == len;
+            if (int rc = run_pass_snap(ctx, last ? PASS_MACROS_T : PASS_STATE | PASS_MACROS_T, sj,
+                                       last ? nullptr : sj + a->slot, sj + a->snap))
                 return rc;
-        // reverse through it, reading each state where it lies
+        }
+        // reverse through it, reading each state and its moments where they lie
         for (int j = len - 1; j >= 0; --j) {
-            const char *sj = a->seg + (size_t)j * a->snap;
-            if (int rc = run_pass_snap(ctx, PASS_MACROS, sj, nullptr, phi, p, u, mu)) return rc;
-            CK(adj_d2q9_step(a->real, &ctx->pd, nx, ny, sj, sj + ctx->fbytes, phi, mu, p, u,
-                             a->lf[cb], a->lg[cb], a->lS[cb], a->lf[cb ^ 1], a->lg[cb ^ 1],
-                             a->lS[cb ^ 1], a->work, a->dpar, ctx->stream));
+            const char *sj = a->seg + (size_t)j * a->slot;
+            CK(adj_d2q9_step(a->real, params_ptr(ctx), nx, ny, sj, sj + ctx->fbytes, sj + a->snap,
+                             a->lf[cb], a->lpt, a->lg[cb], a->lS[cb], a->lf[cb ^ 1],
+                             a->lg[cb ^ 1], a->lS[cb ^ 1], a->work, a->dpar, ctx->stream));
             cb ^= 1;
         }
     }
     // initial condition f = f^eq(phi0, mu(phi0))
     double *lphi0 = on_device ? dL_dphi0 : a->macro;
-    CK(adj_d2q9_init(a->real, &ctx->pd, nx, ny, a->phi0, a->lf[cb], a->work, lphi0, a->dpar,
-                     ctx->stream));
+    CK(adj_d2q9_init(a->real, params_ptr(ctx), nx, ny, a->phi0, a->lf[cb], a->lpt, a->work, lphi0,
+                     a->dpar, ctx->stream));
     double dp[3];
     CK(cudaMemcpyAsync(dp, a->dpar, sizeof dp, cudaMemcpyDeviceToHost, ctx->stream));
     if (!on_device)

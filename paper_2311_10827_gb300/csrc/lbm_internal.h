@@ -32,6 +32,8 @@ enum : int {
     PASS_STATE = 1,   // write post-collision f*, g* and S (a time step)
     PASS_MACROS = 2,  // write phi, p, u, mu (FP64)
     PASS_DIAG = 4,    // per-CTA diagnostics partials
+    PASS_MACROS_T = 8,  // write phi, p, u, mu in the storage type (D2Q9 only;
+                        // alone or with PASS_STATE: the moments of the source state)
 };
 
 struct PassArgs {
@@ -42,6 +44,7 @@ struct PassArgs {
     void *S;              // S_prev in
     void *S_out;          // S out (same node; may equal S: in place)
     double *out_phi, *out_p, *out_u, *out_mu;
+    void *mt_phi, *mt_p, *mt_u, *mt_mu;  // PASS_MACROS_T: all four, storage type
     DiagPartial *partials;
     // FP32 equilibrium shift a (see below): of the source buffer, of the
     // destination buffer (written by the step) and the target for new writes
@@ -160,15 +163,20 @@ cudaError_t offset_refresh(int codec, long long N, int Q, const void *f, const v
 // (the FP64 form) and FP32 when real == 1 (the FP32 form); the forward
 // moments (phi, mu, p, u) are FP64; dpar accumulates in FP64
 // {dL/dkappa, dL/dbeta, dL/d(1/tau_f)}.
-cudaError_t adj_d2q9_seed(int real, int N, const double *dphi, void *lf, void *lg, void *lS,
+// The adjoint of f is lf[i] + lpt (lpt [N]: the part common to every
+// direction, the adjoint of phi = sum_i f_i); a step reads and rewrites lpt.
+cudaError_t adj_d2q9_seed(int real, int N, const double *dphi, void *lf, void *lpt, void *lg,
+                          void *lS, cudaStream_t st);
+// real: 0 FP64, 1 FP32 (the context's storage type R); params: StepParams<R>;
+// moments: phi, mu, p (N each) and u (2N) of the forward state, in R, as
+// the PASS_MACROS_T pass writes them.
+cudaError_t adj_d2q9_step(int real, const void *params, int nx, int ny, const void *f,
+                          const void *g, const void *moments, const void *lf_in, void *lpt,
+                          const void *lg_in, const void *lS_in, void *lf_out, void *lg_out,
+                          void *lS_out, void *work, double *dpar, cudaStream_t st);
+cudaError_t adj_d2q9_init(int real, const void *params, int nx, int ny, const double *phi0,
+                          const void *lf, const void *lpt, void *work, double *lphi0, double *dpar,
                           cudaStream_t st);
-cudaError_t adj_d2q9_step(int precision, const void *params64, int nx, int ny, const void *f,
-                          const void *g, const double *phi, const double *mu, const double *p,
-                          const double *u, const void *lf_in, const void *lg_in, const void *lS_in,
-                          void *lf_out, void *lg_out, void *lS_out, void *work, double *dpar,
-                          cudaStream_t st);
-cudaError_t adj_d2q9_init(int real, const void *params64, int nx, int ny, const double *phi0,
-                          const void *lf, void *work, double *lphi0, double *dpar, cudaStream_t st);
 
 // diagnostics reduction (kernels_diag.cu): partials[n] -> out (one record)
 cudaError_t diag_reduce(const DiagPartial *partials, int n, DiagPartial *out, cudaStream_t st);
