@@ -21,6 +21,13 @@ before.  `e2e` is wall-clock through the C ABI with host buffers: pinned host
 phi0 uploaded by lbm_init_phi, the same steps and diagnostics read-backs, the
 final fields of both grids read back by lbm_moments.
 
+Other workloads (--workload): ensemble (the 256-grid batch), coalescence3d
+(the 512^3 D3Q19 run, --precision fp32 | f16off | bf16off) and adjoint (the
+512^2 gradient).  Each line carries the same measurement keys: `roofline`
+(algorithmic bytes over device time), `e2e` (through the C ABI with host
+buffers), `clocks`, `gpu_launches` and `cpu_baseline` (the oracle on a
+bounded sample of that workload).
+
 Multi-GPU: replicas only (every rank runs its own pair of grids, weak
 scaling; the only collectives are the timing barrier and max).
 
@@ -176,6 +183,90 @@ def cpu_baseline(steps=None, budget_s=12.0):
     return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"{n} time steps of one 1024x1024 D2Q9 droplet grid (rho ratio 10), FP64, "
                       f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def cpu_baseline_ensemble(budget_s=12.0, steps_each=5):
+    """FP64 oracle on the ensemble's own grids in seed order (each initialised,
+    then advanced steps_each time steps, only the steps timed) until the
+    budget is spent."""
+    from oracle import oracle as O
+    from paper_2311_10827_gb300 import workloads as wl
+    O.build()
+    base = wl.physical(wl.DROPLET_1024)
+    updates, dt, k = 0, 0.0, 0
+    while dt < budget_s and k < 256:
+        c = wl.ensemble_case(k)
+        o = O.Oracle((c["n"], c["n"]), **dict(base, rho_l=c["rho_ratio"] * base["rho_v"]))
+        o.init_phi(wl.droplet(c["n"], c["n"], c["R"], base["W"]))
+        t = time.perf_counter()
+        o.step(steps_each)
+        dt += time.perf_counter() - t
+        o.close()
+        updates += c["n"] * c["n"] * steps_each
+        k += 1
+    return {"value": updates / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps_each} time steps of each of the ensemble's grids 0..{k - 1} "
+                      f"(seeds 0..{k - 1}), FP64, single-threaded C oracle, {dt:.1f} s"}
+
+
+def cpu_baseline_coalescence3d(budget_s=12.0):
+    """FP64 oracle (D3Q19) on the workload scaled to 64^3 (R = 8, same W,
+    gap and parameters), as many time steps as fit the budget."""
+    from oracle import oracle as O
+    from paper_2311_10827_gb300 import workloads as wl
+    O.build()
+    cfg = wl.COALESCENCE_3D_SMALL
+    n = cfg["shape"][0]
+    o = O.Oracle((n, n, n), "D3Q19", **wl.physical(cfg))
+    o.init_phi(wl.two_droplets(n, n, cfg["R"], cfg["W"], gap=cfg["gap"], nz=n))
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} time steps of the two-droplet coalescence scaled to {n}^3 "
+                      f"(R = {cfg['R']:g}), D3Q19, FP64, single-threaded C oracle, {dt:.1f} s"}
+
+
+def cpu_baseline_adjoint(budget_s=12.0, n=128, steps=40):
+    """FP64 oracle adjoint (forward run, then the reverse sweep) on the
+    differentiated workload scaled to n^2 (R and the gap scaled, same W and
+    parameters), gradients of steps-step runs repeated until the budget is
+    spent; value in node updates of the differentiated run per second."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2311_10827_gb300 import workloads as wl
+    O.build()
+    cfg = wl.COALESCENCE_ADJ
+    prm = wl.physical(cfg)
+    R = cfg["R"] * n / cfg["shape"][0]
+    phi0 = wl.two_droplets(n, n, R, cfg["W"])
+    target = phi0 + 1e-3 * np.random.default_rng(0).standard_normal(phi0.shape)
+    runs, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        O.phi_loss_gradients((n, n), prm, phi0, target, steps)
+        runs += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps * runs / dt / 1e6, "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{runs} gradients of {steps}-step runs of the two-droplet coalescence "
+                      f"scaled to {n}x{n} (R = {R:g}), FP64 forward + adjoint, "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def adjoint_bytes_per_node(esz):
+    """Algorithmic bytes per node update of the differentiated run: the
+    recorded forward step, the segment recomputation (which also writes the
+    five moments), adj_local, adj_mu and adj_phi (own-node values only;
+    checkpoint copies, 2 % of the bytes at K = 100, are not counted)."""
+    lo = 1 if esz == 4 else 0              # FP32 rest-pair low word
+    fwd = (18 + lo) * 2 * esz + 2 * esz    # f, g (+ lo) read and written, S
+    rec = fwd + 5 * esz                    # + phi, mu, p, ux, uy written
+    local = (18 + lo + 5 + 10 + 9 + 1) * esz + 25 * esz
+    return fwd + rec + local + 4 * esz + 6 * esz
 
 
 def run_reference(args, rank, world, budget_s=90.0, est_mlups=2.0):
@@ -410,33 +501,74 @@ def run_ensemble(args, rank, world, local_rank):
     for i, phi in enumerate(phis):
         b.case(i).init_phi(phi)
     width, rows = b.tune()
-    b.step(args.warmup)
-    torch.cuda.synchronize()
+    ctas = b.shape()[2]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        b.step(args.warmup)
+        torch.cuda.synchronize()
+        t_start = time.time()
+        e0.record(stream)
+        b.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_end = time.time()
     dt = max_over_ranks_dist(e0.elapsed_time(e1) / 1e3, world, dev)
+    b.close()
     nodes = sum(sh[0] * sh[1] for sh, _ in cases)
+
+    # end to end through the C ABI with host buffers: every grid's phi0 from
+    # pinned host memory, the same steps, every grid's final phi to host
+    import numpy as np
+
+    from paper_2311_10827_gb300 import capi
+    hphi = [torch.tensor(p, dtype=torch.float64).pin_memory() for p in phis]
+    hout = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for p in phis]
+    eb = Batch(cases, precision=args.precision, stream=stream.cuda_stream)
+    eb.set_shape(width, rows)  # the tuned shape (tuning is one-time setup)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(len(eb)):
+        capi.check(capi.lbm_init_phi(eb.case(i).handle, hphi[i].numpy(), 0))
+    capi.check(capi.lbm_batch_step(eb.handle, args.steps))
+    for i in range(len(eb)):
+        capi.check(capi.lbm_moments(eb.case(i).handle, hout[i].numpy(), None, None, None, 0))
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    eb.close()
+    if not all(np.isfinite(o.numpy()).all() for o in hout):
+        raise RuntimeError("non-finite phi in the end-to-end run")
     peaks, src = measured_peaks()
     bpn = BYTES_PER_NODE[args.precision]
     if rank == 0:
         v = nodes * args.steps * world / dt / 1e6
-        print(json.dumps({
+        line = {
             "metric": "MLUPS (fused f+g step)", "value": v, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "batched ensemble: 256 stationary 2D droplets, grids "
                                    "64^2..512^2, seeds 0..255", "nodes_per_step": nodes,
-                       "tile": {"width": width, "rows": rows, "ctas": b.shape()[2]}},
+                       "tile": {"width": width, "rows": rows, "ctas": ctas},
+                       "l2": "inputs larger than L2: 27.5M nodes, 2.2 GB read per step"},
             "roofline": {"bound": "hbm", "achieved": bpn * v * 1e6 / 1e9 / world,
                          "peak": peaks["hbm_gbs"],
                          "frac": bpn * v * 1e6 / 1e9 / world / peaks["hbm_gbs"], "unit": "GB/s",
-                         "traffic": None, "peak_source": f"{src} copy bandwidth (hbm_gbs)"}}),
-              flush=True)
-    b.close()
+                         "traffic": None, "peak_source": f"{src} copy bandwidth (hbm_gbs)",
+                         "algorithmic_bytes_per_node": bpn,
+                         "kernel": "d2q9_batch_kernel (all 256 grids per launch)"},
+            "e2e": {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 8 * nodes / args.steps,
+                    "d2h_bytes_per_step": 8 * nodes / args.steps,
+                    "how": "wall clock through the C ABI: lbm_init_phi of every grid from "
+                           "pinned host phi0, lbm_batch_step (tuned shape set before the "
+                           "region), lbm_moments of every grid's phi to pinned host memory"},
+            # one batched launch per step (graph replay), no diagnostics in the region
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(t_start, t_end),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_ensemble()
+        print(json.dumps(line), flush=True)
 
 
 def run_coalescence3d(args, rank, world, local_rank):
@@ -470,6 +602,7 @@ def run_coalescence3d(args, rank, world, local_rank):
         del d
     phi = (0.5 + 0.5 * phi).contiguous()
     sim.init_phi(phi)
+    hphi = phi.cpu().pin_memory()  # host copy for the end-to-end run
     del phi
     torch.cuda.empty_cache()
     plan = []
@@ -503,12 +636,34 @@ def run_coalescence3d(args, rank, world, local_rank):
     step_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps
     nodes = n ** 3
     sim.close()
+
+    # end to end through the C ABI with host buffers: phi0 from pinned host
+    # memory, the same steps and diagnostics read-backs, the final phi to host
+    esim = Simulation((n, n, n), lattice="D3Q19", precision=args.precision,
+                      stream=stream.cuda_stream, **wl.physical(cfg))
+    hout = torch.empty_like(hphi).pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    capi.check(capi.lbm_init_phi(esim.handle, hphi.numpy(), 0))
+    n_diag = 0
+    for m in plan:
+        capi.check(capi.lbm_step(esim.handle, m))
+        rc, d = capi.lbm_diagnostics(esim.handle)  # device -> host read
+        capi.check(rc)
+        n_diag += 1
+    capi.check(capi.lbm_moments(esim.handle, hout.numpy(), None, None, None, 0))
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    esim.close()
+    if not bool(torch.isfinite(hout).all()):
+        raise RuntimeError("non-finite phi in the end-to-end run")
+    del hphi, hout
     if rank != 0:
         return
     peaks, src = measured_peaks()
     bpn = BYTES_PER_NODE_3D[args.precision]
     achieved = bpn * nodes / step_s / 1e9
-    print(json.dumps({
+    line = {
         "metric": "MLUPS (fused f+g step)", "value": nodes * args.steps * world / total_s / 1e6,
         "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -525,6 +680,13 @@ def run_coalescence3d(args, rank, world, local_rank):
                      "algorithmic_bytes_per_node": bpn, "step_ms": step_s * 1e3,
                      "kernel": ("d3q19_off_phi_kernel + d3q19_off_pass_kernel" if "off" in args.precision
                                 else "d3q19_phi_kernel + d3q19_pass_kernel") + " (whole step)"},
+        "e2e": {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 8 * nodes / args.steps,
+                "d2h_bytes_per_step": (8 * nodes + n_diag * ctypes_sizeof_diag()) / args.steps,
+                "how": "wall clock through the C ABI: lbm_init_phi from pinned host phi0, "
+                       "lbm_step in chunks of diag_every steps each followed by "
+                       "lbm_diagnostics (device-to-host read), final phi by lbm_moments to "
+                       "pinned host memory"},
         "mass_drift_rel": (d_last["sum_phi"] - d_first["sum_phi"]) / d_first["sum_phi"],
         "u_max_final": d_last["u_max"],
         "clocks": clk.summary(t_start, t_end),
@@ -532,7 +694,10 @@ def run_coalescence3d(args, rank, world, local_rank):
         # reduction) plus the FP32 shift update or the offset-scale refresh
         "gpu_launches": 2 * args.steps + len(plan) * (
             4 if args.precision == "fp32" else (6 if "off" in args.precision else 3)),
-    }), flush=True)
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_coalescence3d()
+    print(json.dumps(line), flush=True)
 
 
 def run_adjoint(args, rank, world, local_rank):
@@ -576,12 +741,20 @@ def run_adjoint(args, rank, world, local_rank):
         L.backward()
         return float(L.detach()), x.grad, float(sg.grad), float(mo.grad)
 
+    stream = torch.cuda.current_stream()  # the library runs on it (adjoint.rollout)
     one()  # warm-up (builds graphs, touches allocations)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    L, g0, gs, gm = one()
-    torch.cuda.synchronize()
-    t_grad = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        t_start = time.time()
+        t = time.perf_counter()
+        e0.record(stream)
+        L, g0, gs, gm = one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_grad = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+        t_end = time.time()
+    dev_s = max_over_ranks_dist(e0.elapsed_time(e1) / 1e3, world, dev)
     fs = Simulation((nx, ny), precision=args.precision, sigma=sigma0, M=M0, **prm)
     fs.init_phi(phi0)
     fs.step(args.warmup)
@@ -591,26 +764,83 @@ def run_adjoint(args, rank, world, local_rank):
     fs.sync()
     t_fwd = max_over_ranks_dist(time.perf_counter() - t, world, dev)
     fs.close()
+
+    # end to end through the C ABI with host buffers: phi0 from pinned host
+    # memory, the final phi to host, dL/dphi = 2 (phi_N - target) on the host,
+    # the backward pass from and to host memory
+    import numpy as np
+
+    from paper_2311_10827_gb300 import capi
+    hphi0 = torch.tensor(phi0).pin_memory()
+    hphiN = torch.empty_like(hphi0).pin_memory()
+    hdl = torch.empty_like(hphi0).pin_memory()
+    hgrad = torch.empty_like(hphi0).pin_memory()
+    htarget = target.cpu().numpy()
+    es = Simulation((nx, ny), precision=args.precision, stream=stream.cuda_stream, sigma=sigma0,
+                    M=M0, **prm)
+    rc, ha = capi.lbm_adjoint_create(es.handle, 100, nsteps)
+    capi.check(rc, "lbm_adjoint_create")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    capi.check(capi.lbm_adjoint_forward(ha, hphi0.numpy(), 0, nsteps))
+    capi.check(capi.lbm_moments(es.handle, hphiN.numpy(), None, None, None, 0))
+    np.multiply(2.0, hphiN.numpy() - htarget, out=hdl.numpy())
+    rc, eg = capi.lbm_adjoint_backward(ha, hdl.numpy(), 0, hgrad.numpy())
+    capi.check(rc, "lbm_adjoint_backward")
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    capi.lbm_adjoint_destroy(ha)
+    es.close()
+    if not np.isfinite(hgrad.numpy()).all():
+        raise RuntimeError("non-finite gradient in the end-to-end run")
     if rank != 0:
         return
     nodes = nx * ny
-    print(json.dumps({
+    peaks, src = measured_peaks()
+    bpn = adjoint_bytes_per_node(4 if args.precision == "fp32" else 8)
+    achieved = bpn * nodes * nsteps / dev_s / 1e9
+    line = {
         "metric": "MLUPS (fused f+g step), differentiated: forward + adjoint",
         "value": nodes * nsteps * world / t_grad / 1e6, "unit": "MLUPS", "n_gpus": world,
-        "steps": nsteps, "warmup": 1, "ms_per_step": t_grad / nsteps * 1e3,
+        "steps": nsteps, "warmup": nsteps, "ms_per_step": t_grad / nsteps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic",
         "config": {"workload": f"2D two-droplet coalescence {nx}x{ny}, R=48, W=8, "
                                "sigma=5e-3, M=0.1, rho_l/rho_v=10, nu_l/nu_v=1; loss = "
                                "sum (phi_N - phi_target)^2, target from phi0 + 1e-3 N(0,1) "
-                               "(default_rng(0)); checkpoint every 100 steps"},
+                               "(default_rng(0)); checkpoint every 100 steps",
+                   "warmup": "one whole gradient of the same run before the timed one",
+                   "l2": "one step's state (2 x 21 MB) and adjoint fields fit the 129 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": f"{src} copy bandwidth (hbm_gbs)",
+                     "algorithmic_bytes_per_node": bpn, "device_s": dev_s,
+                     "kernel": "whole gradient (recorded forward, segment recomputation with "
+                               "moments, adj_local + adj_mu + adj_phi per reverse step); one "
+                               "step's data (2 x 21 MB) fits the 129 MB L2"},
+        "e2e": {"value": nodes * nsteps * world / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 2 * 8 * nodes / nsteps,
+                "d2h_bytes_per_step": (2 * 8 * nodes + 32) / nsteps,
+                "how": "wall clock through the C ABI: lbm_adjoint_forward from pinned host "
+                       "phi0, lbm_moments of the final phi to host, dL/dphi on the host, "
+                       "lbm_adjoint_backward from and to host memory"},
         "gradient_s": t_grad, "forward_only_s": t_fwd,
         "plain_step_MLUPS": nodes * nsteps / t_fwd / 1e6,
         "cost_vs_plain_forward": t_grad / t_fwd,
         "loss": L, "dL_dsigma": gs, "dL_dM": gm,
         "dL_dphi0_norm": float(g0.norm()),
-    }), flush=True)
+        "e2e_dL_dsigma": eg[0],
+        "clocks": clk.summary(t_start, t_end),
+        # per gradient: initial condition (2), nsteps recorded steps, the
+        # final phi (1), the seed, nsteps recomputation passes (one
+        # moments-only per segment among them), 3 reverse kernels per step,
+        # the initial-condition reverse (2)
+        "gpu_launches": 5 * nsteps + 6,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_adjoint()
+    print(json.dumps(line), flush=True)
 
 
 def max_over_ranks_dist(x, world, device):
