@@ -1339,7 +1339,7 @@ struct lbm_adjoint {
     double *phi0;       // N
     void *lf[2], *lg[2], *lS[2];  // adjoint fields at the adjoint precision
     void *lpt;                    // the adjoint of f common to all directions [N]
-    double *macro;      // 5N doubles (host-resident dL/dphi0 staging)
+    double *macro;      // N doubles: device staging of dL/dphi0 for a host destination
     void *work;         // 7N adjoint values (at least N doubles)
     double *dpar;       // 3
 };
@@ -1404,7 +1404,7 @@ int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_ad
     bool ok = cudaMalloc((void **)&a->ckpt, nck * a->snap) == cudaSuccess &&
               cudaMalloc((void **)&a->seg, (size_t)checkpoint_every * a->slot) == cudaSuccess &&
               cudaMalloc((void **)&a->phi0, N * sizeof(double)) == cudaSuccess &&
-              cudaMalloc((void **)&a->macro, 5 * N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&a->macro, N * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&a->work, 7 * N * a->rsz) == cudaSuccess &&
               cudaMalloc(&a->lpt, N * a->rsz) == cudaSuccess &&
               cudaMalloc((void **)&a->dpar, 3 * sizeof(double)) == cudaSuccess;
