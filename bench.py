@@ -31,6 +31,10 @@ bounded sample of that workload).
 Multi-GPU: replicas only (every rank runs its own pair of grids, weak
 scaling; the only collectives are the timing barrier and max).
 
+`cpu_baseline` is the FP64 oracle on one host core on a bounded sample of the
+workload; `cpu_baseline_all_cores` runs one oracle process per host core.
+--size 4096 runs the same line on two 4096 x 4096 grids (the out-of-L2 point).
+
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (rank 0 only).
 """
@@ -59,8 +63,12 @@ BYTES_PER_NODE_3D = {"fp32": 320, "fp64": 624, "f16off": 208, "bf16off": 208}
 DTYPE = {"fp32": "f32", "fp64": "f64", "f16off": "f32 (f16 offset storage)",
          "bf16off": "f32 (bf16 offset storage)"}
 KERNEL_SOURCES = ("paper_2311_10827_gb300/csrc/kernels_d2q9.cu",)
-TRAFFIC_KERNEL = "d2q9_batch_kernel"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_d2q9_fp32_droplet1024.txt")
+# DRAM bytes per step of the default line's kernel, from committed ncu
+# summaries: the per-step launch and the multi-step cooperative launch
+TRAFFIC_FILES = {
+    "per_step": os.path.join(ROOT, "profiles", "traffic_d2q9_fp32_droplet1024.txt"),
+    "multi_step": os.path.join(ROOT, "profiles", "traffic_d2q9_persist_fp32_droplet1024.txt"),
+}
 
 
 def params(ratio):
@@ -70,9 +78,10 @@ def params(ratio):
     return p
 
 
-def phi0():
+def phi0(n=NX):
+    """The droplet on an n x n grid, R = 128 n / 1024 (R/L = 1/8)."""
     from paper_2311_10827_gb300 import workloads as wl
-    return wl.droplet(NX, NY, wl.DROPLET_1024["R"], wl.DROPLET_1024["W"])
+    return wl.droplet(n, n, wl.DROPLET_1024["R"] * n / NX, wl.DROPLET_1024["W"])
 
 
 def measured_peaks():
@@ -91,19 +100,19 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
-    on the kernel source as it is now."""
+def ncu_traffic(mode="per_step"):
+    """DRAM bytes per step from the committed ncu summary of the kernel that
+    ran, if it was taken on the kernel source as it is now."""
     try:
         kv = {}
-        with open(TRAFFIC_FILE) as fh:
+        with open(TRAFFIC_FILES[mode]) as fh:
             for line in fh:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_sha") != kernel_hash():
             return None
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_step"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -183,6 +192,52 @@ def cpu_baseline(steps=None, budget_s=12.0):
     return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"{n} time steps of one 1024x1024 D2Q9 droplet grid (rho ratio 10), FP64, "
                       f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def _oracle_worker(budget_s, barrier, out):
+    """One oracle process of the all-cores timing: its own 1024 x 1024 grid
+    (rho ratio 10), time steps until the budget is spent after a common start."""
+    from oracle import oracle as O
+    o = O.Oracle((NX, NY), **params(RATIOS[0]))
+    o.init_phi(phi0())
+    o.step(1)
+    barrier.wait()
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        o.step(1)
+        n += 1
+    out.put((n, time.perf_counter() - t0))
+
+
+def cpu_baseline_all_cores(budget_s=10.0):
+    """The oracle on every host core at once: one single-threaded process per
+    core (spawned), each stepping its own 1024 x 1024 grid; value = all node
+    updates over the longest process's stepping time."""
+    import multiprocessing as mp
+
+    from oracle import oracle as O
+    O.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(budget_s, barrier, out)) for _ in range(cores)]
+    for pr in procs:
+        pr.start()
+    try:
+        res = [out.get(timeout=budget_s + 300) for _ in procs]
+    except Exception as e:  # a worker that died never reports
+        for pr in procs:
+            pr.terminate()
+        return {"unavailable": f"all-cores oracle run failed: {type(e).__name__}"}
+    for pr in procs:
+        pr.join()
+    steps = sum(n for n, _ in res)
+    dt = max(t for _, t in res)
+    return {"value": NX * NY * steps / dt / 1e6, "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{cores} single-threaded oracle processes, each stepping its own "
+                      f"1024x1024 D2Q9 droplet grid (rho ratio 10), FP64, {steps} time steps "
+                      f"in all over {dt:.1f} s"}
 
 
 def cpu_baseline_ensemble(budget_s=12.0, steps_each=5):
@@ -315,6 +370,7 @@ def run_native(args, rank, world, local_rank):
     from paper_2311_10827_gb300 import build as B
     B.build()
     from paper_2311_10827_gb300 import capi
+    from paper_2311_10827_gb300 import workloads as wl
     from paper_2311_10827_gb300.sim import Batch
 
     dev = torch.device("cuda", local_rank)
@@ -322,7 +378,9 @@ def run_native(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     prec = args.precision
     de = args.diag_every
-    cases = [((NX, NY), params(r)) for r in RATIOS]
+    n = args.size or NX  # grid edge (1024: the headline; 4096: the out-of-L2 point)
+    R = wl.DROPLET_1024["R"] * n / NX
+    cases = [((n, n), params(r)) for r in RATIOS]
 
     def barrier():
         if world > 1:
@@ -341,7 +399,7 @@ def run_native(args, rank, world, local_rank):
 
     # ---- device-resident timing: one batched launch per step over both grids
     batch = Batch(cases, precision=prec, stream=stream.cuda_stream)
-    phi_d = torch.tensor(phi0(), dtype=torch.float64, device=dev)
+    phi_d = torch.tensor(phi0(n), dtype=torch.float64, device=dev)
     for i in range(len(batch)):
         batch.case(i).init_phi(phi_d)
     if args.tile:
@@ -349,6 +407,15 @@ def run_native(args, rank, world, local_rank):
         batch.set_shape(width, rows)
     else:
         width, rows = batch.tune()
+    multi = False
+    if not args.per_step:
+        # one cooperative launch per chunk of steps when every tile of the
+        # tuned shape fits the GPU at once (bit-identical to per-step launches)
+        try:
+            batch.set_persistent(True)
+            multi = True
+        except capi.LbmError:
+            pass
     plan = chunks(args.steps)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in plan]
@@ -374,19 +441,22 @@ def run_native(args, rank, world, local_rank):
         t_wall = time.perf_counter() - t_wall
         t_end = time.time()
     total_s = max_over_ranks(t0.elapsed_time(t1) / 1e3)
-    kernel_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps  # per batched launch
-    nodes = NX * NY * len(cases)
+    kernel_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps  # per step
+    nodes = n * n * len(cases)
     value = nodes * args.steps * world / total_s / 1e6
     ntiles = batch.shape()[2]
     batch.close()
 
     # ---- end to end through the C ABI with host buffers
-    hphi = torch.tensor(phi0(), dtype=torch.float64).pin_memory()
+    hphi = torch.tensor(phi0(n), dtype=torch.float64).pin_memory()
     hphi_np = hphi.numpy()
-    outs = [dict(phi=np.empty(NX * NY), p=np.empty(NX * NY), mu=np.empty(NX * NY),
-                 u=np.empty(2 * NX * NY)) for _ in cases]
+    out_t = [{k: torch.empty(m * n * n, dtype=torch.float64).pin_memory()
+              for k, m in (("phi", 1), ("p", 1), ("mu", 1), ("u", 2))} for _ in cases]
+    outs = [{k: t.numpy() for k, t in o.items()} for o in out_t]  # views of pinned memory
     eb = Batch(cases, precision=prec, stream=stream.cuda_stream)
     eb.set_shape(width, rows)  # the tile shape tuned above (tuning is one-time setup)
+    if multi:
+        eb.set_persistent(True)
     barrier()
     t_e = time.perf_counter()
     for i in range(len(eb)):
@@ -405,8 +475,8 @@ def run_native(args, rank, world, local_rank):
     eb.close()
     e2e_value = nodes * args.steps * world / e2e_s / 1e6
     diag_bytes = ctypes_sizeof_diag()
-    h2d = NX * NY * 8 * len(cases) / args.steps
-    d2h = (n_diag_reads * diag_bytes + 5 * NX * NY * 8 * len(cases)) / args.steps
+    h2d = n * n * 8 * len(cases) / args.steps
+    d2h = (n_diag_reads * diag_bytes + 5 * n * n * 8 * len(cases)) / args.steps
 
     if rank != 0:
         return
@@ -438,25 +508,32 @@ def run_native(args, rank, world, local_rank):
     peaks, src = measured_peaks()
     bpn = BYTES_PER_NODE[prec]
     achieved = bpn * nodes / kernel_s / 1e9
-    traffic = ncu_traffic() if prec == "fp32" else None
+    traffic = (ncu_traffic("multi_step" if multi else "per_step")
+               if prec == "fp32" and n == NX else None)
     line = {
         "metric": "MLUPS (fused f+g step)", "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
         "data": "synthetic",
-        "config": {"workload": "2D stationary droplet 1024x1024 periodic, R=128, W=4, "
+        "config": {"workload": f"2D stationary droplet {n}x{n} periodic, R={R:g}, W=4, "
                                "sigma=1e-3, M=0.05, nu_l/nu_v=10, rho_l/rho_v=10 and 100 "
                                "(one step = both grids, one batched launch)",
                    "lattice": "D2Q9", "nodes_per_step": nodes, "diag_every": de,
                    "tile": {"width": width, "rows": rows, "ctas": ntiles},
-                   "l2": "inputs larger than L2: 2 x 84 MB read per step, back to back",
+                   "launch": ("one cooperative launch per chunk of steps, each tile "
+                              "synchronised with its neighbours" if multi
+                              else "one launch per step, CUDA-graph replay"),
+                   "l2": f"inputs larger than L2: 2 x {80 * n * n / 1e6:.0f} MB read per step, "
+                         "back to back",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": traffic, "peak_source": f"{src} copy bandwidth (hbm_gbs)",
                      "algorithmic_bytes_per_node": bpn, "kernel_ms": kernel_s * 1e3,
-                     "kernel": "d2q9_batch_kernel (both grids per launch)"},
+                     "kernel": ("d2q9_batch_persist_kernel (both grids, diag_every steps per "
+                                "launch; per-step time and traffic)" if multi
+                                else "d2q9_batch_kernel (both grids per launch)")},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "how": "wall clock through the C ABI: lbm_init_phi from pinned host phi0, "
@@ -467,12 +544,15 @@ def run_native(args, rank, world, local_rank):
         "accuracy": accuracy,
         # one step kernel per step; per chunk and grid the diagnostics pass,
         # its reduction and (FP32) the equilibrium-shift update
-        "gpu_launches": args.steps + len(plan) * len(cases) * (3 if prec == "fp32" else 2),
+        # multi-step: per chunk the cooperative launch and the shift record
+        "gpu_launches": (2 * len(plan) if multi else args.steps)
+        + len(plan) * len(cases) * (3 if prec == "fp32" else 2),
         "clocks": clk.summary(t_start, t_end),
         "wall_s_timed_region": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
     print(json.dumps(line), flush=True)
 
 
@@ -873,6 +953,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP64 comparison run after the timed region (profiling)")
+    ap.add_argument("--per-step", action="store_true",
+                    help="droplet1024: one launch per step even when the tuned tiles fit the GPU "
+                         "at once (default there: one cooperative launch per chunk of steps)")
     ap.add_argument("--tile", default="", help="WxR: fixed batch tile shape instead of the "
                     "autotuner (profiling commands use the shape the tuner picked)")
     ap.add_argument("--workload", choices=["droplet1024", "ensemble", "coalescence3d", "adjoint"],
@@ -880,7 +963,8 @@ def main():
                     help="droplet1024: the headline line; ensemble: the 256-grid batch; "
                          "coalescence3d: the 512^3 D3Q19 run; adjoint: the 512^2 gradient")
     ap.add_argument("--size", type=int, default=0,
-                    help="coalescence3d: edge of the cube (default 512)")
+                    help="droplet1024: edge of the square grids (default 1024; 4096 is the "
+                         "out-of-L2 point); coalescence3d: edge of the cube (default 512)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

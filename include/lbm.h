@@ -318,6 +318,29 @@ int lbm_batch_shape(const lbm_batch *b, int *width, int *rows, int *ntiles);
  * lbm_batch_step calls do not tune.  Errors: INVALID_ARG, OOM, CUDA. */
 int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
 
+/* Multi-step launches.  With on = 1, an lbm_batch_step call of n >= 2 steps
+ * runs as ONE cooperative launch in which every tile keeps its CTA for all n
+ * steps.  After each step a tile publishes a per-tile step counter, and before
+ * the next it waits only for the tiles its stencil reaches (3 nodes) to reach
+ * the same step.  Tiles therefore drift apart instead of starting and ending
+ * every step together.  The results are the same, bit for bit, as those of
+ * per-step launches.  It needs every tile of the current shape resident at
+ * once (tiles <= resident CTAs per SM x SMs), so it suits batches whose
+ * tiles fill about one wave.  A wait is bounded (about 2 s of SM clock). On
+ * a timeout the tile sets an error word, fills its region of S with NaN (so
+ * that diagnostics report non-finite fields) and stops; see
+ * lbm_batch_persistent.  Tunes first if the batch is untuned.
+ * on = 0 returns to per-step launches (CUDA-graph replay).
+ * Errors: INVALID_ARG (NULL, or on = 1 with a shape whose tiles do not fit
+ * the GPU at once), CUDA. */
+int lbm_batch_set_persistent(lbm_batch *b, int on);
+
+/* *on (optional): whether multi-step launches are in use.  *timed_out
+ * (optional): whether a multi-step launch has timed out waiting for a
+ * neighbour tile.  Reading timed_out synchronises the device.
+ * Errors: INVALID_ARG, CUDA. */
+int lbm_batch_persistent(const lbm_batch *b, int *on, int *timed_out);
+
 /* Release the batch and all its contexts (synchronises first).  NULL-safe. */
 void lbm_batch_destroy(lbm_batch *b);
 

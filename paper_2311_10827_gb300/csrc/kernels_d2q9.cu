@@ -78,22 +78,31 @@ __device__ __forceinline__ int wrap_row(int r, int n, bool small)
     return r < 0 ? r + n : (r >= n ? r - n : r);
 }
 
+// Load of a population: through the read-only path (NC, data constant for
+// the launch), or from L2 only (data that other CTAs write during the same
+// launch: the multi-step kernel).
+template <bool NC, typename T>
+__device__ __forceinline__ T ldp(const T *p)
+{
+    return NC ? __ldg(p) : __ldcg(p);
+}
+
 // The nine populations arriving at (x, y): v[i] = src_i(x - cx_i, y - cy_i).
 // rm/r0/rp are the offsets of rows y-1, y, y+1; xm/x/xp the wrapped columns.
 // Offsets are 32-bit (Q N < 2^32 is checked at context creation).
-template <typename T>
+template <bool NC, typename T>
 __device__ __forceinline__ void pull9(const T *__restrict__ s, unsigned N, unsigned rm, unsigned r0,
                                       unsigned rp, unsigned xm, unsigned x, unsigned xp, T v[9])
 {
-    v[0] = __ldg(s + (r0 + x));
-    v[1] = __ldg(s + (1u * N + rp + x));   // c = (0,-1) comes from y + 1
-    v[2] = __ldg(s + (2u * N + r0 + xm));  // c = (1,0)  comes from x - 1
-    v[3] = __ldg(s + (3u * N + rm + x));   // c = (0,1)  comes from y - 1
-    v[4] = __ldg(s + (4u * N + r0 + xp));  // c = (-1,0) comes from x + 1
-    v[5] = __ldg(s + (5u * N + rm + xm));  // c = (1,1)
-    v[6] = __ldg(s + (6u * N + rm + xp));  // c = (-1,1)
-    v[7] = __ldg(s + (7u * N + rp + xp));  // c = (-1,-1)
-    v[8] = __ldg(s + (8u * N + rp + xm));  // c = (1,-1)
+    v[0] = ldp<NC>(s + (r0 + x));
+    v[1] = ldp<NC>(s + (1u * N + rp + x));   // c = (0,-1) comes from y + 1
+    v[2] = ldp<NC>(s + (2u * N + r0 + xm));  // c = (1,0)  comes from x - 1
+    v[3] = ldp<NC>(s + (3u * N + rm + x));   // c = (0,1)  comes from y - 1
+    v[4] = ldp<NC>(s + (4u * N + r0 + xp));  // c = (-1,0) comes from x + 1
+    v[5] = ldp<NC>(s + (5u * N + rm + xm));  // c = (1,1)
+    v[6] = ldp<NC>(s + (6u * N + rm + xp));  // c = (-1,1)
+    v[7] = ldp<NC>(s + (7u * N + rp + xp));  // c = (-1,-1)
+    v[8] = ldp<NC>(s + (8u * N + rp + xm));  // c = (1,-1)
 }
 
 // Per-thread asynchronous copy global -> shared (4 or 8 bytes) and its
@@ -112,6 +121,7 @@ __device__ __forceinline__ void cp_wait_all_but_one()
 {
     asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // the nine pull addresses of (x, y) (same order as pull9)
 template <typename T>
@@ -174,7 +184,7 @@ struct Occ {
 // One tile: columns [x0, x0 + TX), rows [y0, yend), marching in direction
 // dir (+1 down from y0, -1 up from yend - 1); diagnostics partial record
 // `part` (PASS_DIAG).  Shared by the single-grid and the batched kernels.
-template <typename T, int TX, int PASS>
+template <typename T, int TX, int PASS, bool NC = true>
 __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs &a, int x0, int y0,
                                           int yend, int dir, int part)
 {
@@ -217,7 +227,7 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
     if (REST_PAIR && (PASS & PASS_STATE)) {
         a_src = *a.eqs_src;
         a_dst = *a.eqs_target;
-        if (x0 == 0 && y0 == 0 && lin == 0) *a.eqs_dst = a_dst;
+        if (a.eqs_dst && x0 == 0 && y0 == 0 && lin == 0) *a.eqs_dst = a_dst;
     }
 
     // m(row) = dir (row - first) is the march coordinate, >= -2 for every row used
@@ -233,13 +243,13 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
         const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
         const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
         const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
-        pull9(fsrc, N, rm, r0, rp, xOm, xO, xOp, v);
-        lo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xO)) : T(0);
+        pull9<NC>(fsrc, N, rm, r0, rp, xOm, xO, xOp, v);
+        lo = REST_PAIR ? ldp<NC>(fsrc + (9u * N + r0 + xO)) : T(0);
         put_phi(sl, tx + 2, v[0], lo + sum_moving(v));
         if (tx < 4) {
             T h[9];
-            pull9(fsrc, N, rm, r0, rp, xHm, xH, xHp, h);
-            const T hlo = REST_PAIR ? __ldg(fsrc + (9u * N + r0 + xH)) : T(0);
+            pull9<NC>(fsrc, N, rm, r0, rp, xHm, xH, xHp, h);
+            const T hlo = REST_PAIR ? ldp<NC>(fsrc + (9u * N + r0 + xH)) : T(0);
             put_phi(sl, jH, h[0], hlo + sum_moving(h));
         }
     };
@@ -331,7 +341,7 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
         {
             const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
             const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
-            pull9(gsrc, N, rm, nrow, rp, xOm, xO, xOp, gv);
+            pull9<NC>(gsrc, N, rm, nrow, rp, xOm, xO, xOp, gv);
             if ((PASS & (PASS_STATE | PASS_DIAG)) && out_ok)
                 Sprev = __ldcs(static_cast<const T *>(a.S) + (nrow + xo));
         }
@@ -506,6 +516,7 @@ __device__ __forceinline__ void d2q9_tile(const StepParams<T> &P, const PassArgs
         for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
         locur = lonext;
     }
+    if (!NC) cp_wait_all();  // the next step of a multi-step launch reuses the stages
 
     if (PASS & PASS_DIAG) {
         warp_reduce(d_phi, d_E, d_u2, d_mumin, d_mumax, d_bud, d_bad);
@@ -585,6 +596,113 @@ __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS, TX>::ctas))
     a.eqs_dst = c.eqs + (parity ^ 1);
     a.eqs_target = c.eqs + 2;
     d2q9_tile<T, TX, PASS>(P, a, t.x0, t.y0, t.yend, parity ? -t.dir : t.dir, blockIdx.x);
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Longest wait of a tile for its neighbours, in SM clock cycles (about 2 s):
+// a correct launch never comes near it (neighbours are at most one step
+// apart and all CTAs are resident: cooperative launch).
+constexpr long long PERSIST_WAIT_CYCLES = 4000000000LL;
+
+// Several time steps of a batch in one cooperative launch, one CTA per tile
+// for the whole launch (every tile resident at once).  After step k a tile
+// publishes flags[tile] = k + 1 (release); before step k + 1 it waits until
+// every tile whose region its stencil reaches (nbr: count, then indices) has
+// published k + 1 (acquire).  Neighbours are then at most one step apart, so
+// a tile never reads a buffer a neighbour is still writing or writes one a
+// neighbour is still reading; no grid-wide barrier is needed, and tiles drift
+// apart instead of starting and ending every step together.  Populations
+// other tiles write in this launch are read through L2 (no read-only path).
+// The FP32 shift of the source buffer is the stored one at step 0 and the
+// target after it (what step 0 wrote with); the caller records the final
+// buffer's shift.  A wait that runs past PERSIST_WAIT_CYCLES sets *err,
+// fills the tile's S with NaN (so the diagnostics report non-finite fields)
+// and ends the CTA; tiles waiting on it then time out too.
+template <typename T, int TX>
+__global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS_STATE, TX>::ctas))
+    d2q9_batch_persist_kernel(const BatchCase *__restrict__ cases, const BatchTile *__restrict__ tiles,
+                              const int *__restrict__ nbr, int parity0, int nsteps, int *flags,
+                              int *err)
+{
+    const BatchTile t = tiles[blockIdx.x];
+    const BatchCase &c = cases[t.c];
+    const StepParams<T> P = *reinterpret_cast<const StepParams<T> *>(
+        sizeof(T) == 4 ? (const void *)&c.pf : (const void *)&c.pd);
+    const int lin = threadIdx.y * TX + threadIdx.x;
+    const int *nb = nbr + (size_t)blockIdx.x * (PERSIST_NBMAX + 1);
+    __shared__ int s_abort;
+    for (int k = 0; k < nsteps; ++k) {
+        if (k > 0) {
+            if (lin < 32) {
+                bool bad = false;
+                if (lin < nb[0]) {
+                    const int *fl = flags + nb[1 + lin];
+                    const long long t0 = clock64();
+                    while (ld_acquire_gpu(fl) < k) {
+                        if (clock64() - t0 > PERSIST_WAIT_CYCLES || ld_acquire_gpu(err) != 0) {
+                            bad = true;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                bad = __any_sync(0xffffffffu, bad);
+                if (lin == 0) {
+                    if (bad) atomicExch(err, 1);
+                    s_abort = bad ? 1 : 0;
+                }
+                __threadfence();  // the polling warp's acquires reach the CTA through the barrier
+            }
+            __syncthreads();
+            if (s_abort) {
+                T *S = static_cast<T *>(c.S);
+                const int x = t.x0 + threadIdx.x;
+                if (x < P.nx)
+                    for (int y = t.y0 + (int)threadIdx.y; y < t.yend; y += TYB)
+                        S[(size_t)y * P.nx + x] = T(NAN);
+                return;
+            }
+        }
+        const int parity = parity0 ^ (k & 1);
+        PassArgs a;
+        a.f_src = c.f[parity];
+        a.f_dst = c.f[parity ^ 1];
+        a.g_src = c.g[parity];
+        a.g_dst = c.g[parity ^ 1];
+        a.S = c.S;
+        a.S_out = c.S;
+        a.out_phi = a.out_p = a.out_u = a.out_mu = nullptr;
+        a.mt_phi = a.mt_p = a.mt_u = a.mt_mu = nullptr;
+        a.partials = nullptr;
+        a.eqs_src = k == 0 ? c.eqs + parity0 : c.eqs + 2;
+        a.eqs_dst = nullptr;
+        a.eqs_target = c.eqs + 2;
+        a.flip = 0;
+        d2q9_tile<T, TX, PASS_STATE, false>(P, a, t.x0, t.y0, t.yend, parity ? -t.dir : t.dir,
+                                            blockIdx.x);
+        __syncthreads();  // every output of the step is stored
+        if (lin == 0) {
+            __threadfence();
+            st_release_gpu(flags + blockIdx.x, k + 1);
+        }
+    }
+}
+
+// the final buffer's FP32 shift after a multi-step launch: the target
+__global__ void d2q9_batch_eqs_final(const BatchCase *__restrict__ cases, int ncases, int parity)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ncases) cases[i].eqs[parity] = cases[i].eqs[2];
 }
 
 // ------------------------------------------------------------ initial state
@@ -722,6 +840,58 @@ cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
                            : launch_batch_t<double, 128>(cases, tiles, ntiles, parity, st);
     return width == 64 ? launch_batch_t<float, 64>(cases, tiles, ntiles, parity, st)
                        : launch_batch_t<float, 128>(cases, tiles, ntiles, parity, st);
+}
+
+namespace {
+
+template <typename T, int TX>
+cudaError_t launch_persist_t(const BatchCase *cases, int ncases, const BatchTile *tiles,
+                             const int *nbr, int ntiles, int parity, int nsteps, int *flags,
+                             int *err, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)ntiles * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&cases, (void *)&tiles, (void *)&nbr, (void *)&parity,
+                    (void *)&nsteps, (void *)&flags, (void *)&err};
+    e = cudaLaunchCooperativeKernel((const void *)d2q9_batch_persist_kernel<T, TX>, dim3(ntiles),
+                                    dim3(TX, TYB), args, 0, st);
+    if (e != cudaSuccess) return e;
+    d2q9_batch_eqs_final<<<(ncases + 127) / 128, 128, 0, st>>>(cases, ncases,
+                                                               parity ^ (nsteps & 1));
+    return cudaGetLastError();
+}
+
+template <typename T, int TX>
+int persist_ctas_per_sm_t()
+{
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, d2q9_batch_persist_kernel<T, TX>, TX * TYB, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+}  // namespace
+
+cudaError_t d2q9_batch_persist(int precision, int width, const BatchCase *cases, int ncases,
+                               const BatchTile *tiles, const int *nbr, int ntiles, int parity,
+                               int nsteps, int *flags, int *err, cudaStream_t st)
+{
+    if (precision == 0)
+        return width == 64 ? launch_persist_t<double, 64>(cases, ncases, tiles, nbr, ntiles,
+                                                          parity, nsteps, flags, err, st)
+                           : launch_persist_t<double, 128>(cases, ncases, tiles, nbr, ntiles,
+                                                           parity, nsteps, flags, err, st);
+    return width == 64 ? launch_persist_t<float, 64>(cases, ncases, tiles, nbr, ntiles, parity,
+                                                     nsteps, flags, err, st)
+                       : launch_persist_t<float, 128>(cases, ncases, tiles, nbr, ntiles, parity,
+                                                      nsteps, flags, err, st);
+}
+
+int d2q9_batch_persist_ctas_per_sm(int precision, int width)
+{
+    if (precision == 0)
+        return width == 64 ? persist_ctas_per_sm_t<double, 64>() : persist_ctas_per_sm_t<double, 128>();
+    return width == 64 ? persist_ctas_per_sm_t<float, 64>() : persist_ctas_per_sm_t<float, 128>();
 }
 
 LaunchShape d2q9_shape(int nx, int ny, int num_sms)

@@ -1002,6 +1002,13 @@ struct lbm_batch {
     cudaGraphExec_t gexec;
     int gexec_valid;
     int err;
+    // multi-step launches (one resident CTA per tile for the whole call)
+    int persist;     // requested
+    int persist_ok;  // the current tiles fit the GPU at once and have neighbour lists
+    int *d_nbr;      // per tile: count, then up to PERSIST_NBMAX neighbour tiles
+    int *d_flags;    // per tile: steps completed in the current launch
+    int *d_err;      // set by a wait that timed out
+    int persist_cap; // tiles d_nbr and d_flags hold
 };
 
 namespace {
@@ -1011,6 +1018,9 @@ constexpr int BATCH_GRAPH_STEPS = 32;
 void batch_free(lbm_batch *b)
 {
     if (b->gexec_valid) cudaGraphExecDestroy(b->gexec);
+    if (b->d_nbr) cudaFree(b->d_nbr);
+    if (b->d_flags) cudaFree(b->d_flags);
+    if (b->d_err) cudaFree(b->d_err);
     if (b->d_cases) cudaFree(b->d_cases);
     if (b->d_cases_tune) cudaFree(b->d_cases_tune);
     if (b->d_tiles) cudaFree(b->d_tiles);
@@ -1033,6 +1043,87 @@ void batch_free(lbm_batch *b)
 
 // tiles of every grid: strips of `width` columns, row tiles of `rows` rows,
 // row-major per grid; odd row tiles march up
+// Neighbour lists of the tiles for multi-step launches: for every tile the
+// other tiles of its grid whose region meets the tile's stencil reach (3
+// nodes: phi at radius 2 is summed from populations pulled at radius 1),
+// periodic.  Sets persist_ok when every tile fits the GPU at once and no list
+// is longer than PERSIST_NBMAX.
+int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int rows)
+{
+    b->persist_ok = 0;
+    const int per_sm = d2q9_batch_persist_ctas_per_sm(b->precision == LBM_FP64 ? 0 : 1, width);
+    if (per_sm < 1 || count > per_sm * b->nsm || rows < 1) return LBM_OK;
+    constexpr int REACH = 3;
+    const int stride = PERSIST_NBMAX + 1;
+    int *nb = (int *)malloc((size_t)count * stride * sizeof(int));
+    if (!nb) return LBM_ERR_OOM;
+    int base = 0;  // index of the case's first tile
+    bool ok = true;
+    for (int k = 0; k < count && ok; ++k) {
+        const BatchTile &t = h[k];
+        if (k > 0 && t.c != h[k - 1].c) base = k;
+        const lbm_grid &g = b->ctx[t.c]->grid;
+        const int sx = (g.nx + width - 1) / width;
+        const int xe = t.x0 + width < g.nx ? t.x0 + width : g.nx;
+        // the distinct tile rows and strips the reach touches, then their product
+        int rs[PERSIST_NBMAX + 1], ss[PERSIST_NBMAX + 1], nr = 0, ns = 0;
+        for (int yy = t.y0 - REACH; yy < t.yend + REACH && ok; ++yy) {
+            const int r = ((yy % g.ny) + g.ny) % g.ny / rows;
+            bool seen = false;
+            for (int j = 0; j < nr; ++j) seen = seen || rs[j] == r;
+            if (!seen) {
+                if (nr == PERSIST_NBMAX + 1) ok = false;
+                else rs[nr++] = r;
+            }
+        }
+        for (int xx = t.x0 - REACH; xx < xe + REACH && ok; ++xx) {
+            const int sidx = ((xx % g.nx) + g.nx) % g.nx / width;
+            bool seen = false;
+            for (int j = 0; j < ns; ++j) seen = seen || ss[j] == sidx;
+            if (!seen) {
+                if (ns == PERSIST_NBMAX + 1) ok = false;
+                else ss[ns++] = sidx;
+            }
+        }
+        int *row = nb + (size_t)k * stride, n = 0;
+        for (int i = 0; i < nr && ok; ++i)
+            for (int j = 0; j < ns && ok; ++j) {
+                const int u = base + rs[i] * sx + ss[j];
+                if (u == k) continue;
+                if (n == PERSIST_NBMAX) ok = false;
+                else row[1 + n++] = u;
+            }
+        row[0] = n;
+    }
+    if (!ok) {
+        free(nb);
+        return LBM_OK;
+    }
+    if (count > b->persist_cap) {
+        if (b->d_nbr) cudaFree(b->d_nbr);
+        if (b->d_flags) cudaFree(b->d_flags);
+        b->d_nbr = nullptr;
+        b->d_flags = nullptr;
+        b->persist_cap = 0;
+        if (cudaMalloc((void **)&b->d_nbr, (size_t)count * stride * sizeof(int)) != cudaSuccess ||
+            cudaMalloc((void **)&b->d_flags, (size_t)count * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            free(nb);
+            return LBM_ERR_OOM;
+        }
+        b->persist_cap = count;
+    }
+    const cudaError_t e =
+        cudaMemcpy(b->d_nbr, nb, (size_t)count * stride * sizeof(int), cudaMemcpyHostToDevice);
+    free(nb);
+    if (e != cudaSuccess) {
+        b->err = LBM_ERR_CUDA;
+        return LBM_ERR_CUDA;
+    }
+    b->persist_ok = 1;
+    return LBM_OK;
+}
+
 int batch_build_tiles(lbm_batch *b, int width, int rows)
 {
     long long count = 0;
@@ -1070,11 +1161,14 @@ int batch_build_tiles(lbm_batch *b, int width, int rows)
         b->tiles_cap = (int)count;
     }
     cudaError_t e = cudaMemcpy(b->d_tiles, h, (size_t)count * sizeof(BatchTile), cudaMemcpyHostToDevice);
-    free(h);
     if (e != cudaSuccess) {
+        free(h);
         b->err = LBM_ERR_CUDA;
         return LBM_ERR_CUDA;
     }
+    const int rc = batch_build_nbr(b, h, (int)count, width, rows);
+    free(h);
+    if (rc) return rc;
     b->ntiles = (int)count;
     b->width = width;
     b->rows = rows;
@@ -1223,7 +1317,9 @@ int lbm_batch_create(int ncases, const lbm_grid *grids, const lbm_params *params
     const size_t bytes = (size_t)ncases * sizeof(BatchCase);
     bool ok = cudaMalloc((void **)&b->d_cases, bytes) == cudaSuccess &&
               cudaMalloc((void **)&b->d_cases_tune, bytes) == cudaSuccess &&
-              cudaMemcpy(b->d_cases, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+              cudaMemcpy(b->d_cases, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_err, sizeof(int)) == cudaSuccess &&
+              cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess;
     for (int c = 0; c < ncases && ok; ++c) h[c].S_out = b->ctx[c]->aux;  // scratch for tuning
     ok = ok && cudaMemcpy(b->d_cases_tune, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1274,6 +1370,13 @@ int lbm_batch_step(lbm_batch *b, int n)
     if (int rc = batch_ready(b)) return rc;
     if (!b->tuned && n > 0)
         if (int rc = batch_tune(b)) return rc;
+    if (b->persist && b->persist_ok && n >= 2) {
+        BK(d2q9_batch_persist(b->precision == LBM_FP64 ? 0 : 1, b->width, b->d_cases, b->n,
+                              b->d_tiles, b->d_nbr, b->ntiles, b->ctx[0]->cur, n, b->d_flags,
+                              b->d_err, b->stream));
+        batch_advance(b, n);
+        return LBM_OK;
+    }
     int left = n;
     if (left >= BATCH_GRAPH_STEPS) {
         if (b->ctx[0]->cur == 1) {
@@ -1311,6 +1414,31 @@ int lbm_batch_set_shape(lbm_batch *b, int width, int rows)
     if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
     if (int rc = batch_build_tiles(b, width, rows)) return rc;
     b->tuned = 1;
+    return LBM_OK;
+}
+
+int lbm_batch_set_persistent(lbm_batch *b, int on)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (on && !b->tuned)
+        if (int rc = batch_tune(b)) return rc;
+    if (on && !b->persist_ok) return LBM_ERR_INVALID_ARG;
+    b->persist = on ? 1 : 0;
+    return LBM_OK;
+}
+
+int lbm_batch_persistent(const lbm_batch *b, int *on, int *timed_out)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (on) *on = b->persist && b->persist_ok;
+    if (timed_out) {
+        int v = 0;
+        if (cudaSetDevice(b->device) != cudaSuccess ||
+            cudaMemcpy(&v, b->d_err, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return LBM_ERR_CUDA;
+        *timed_out = v;
+    }
     return LBM_OK;
 }
 

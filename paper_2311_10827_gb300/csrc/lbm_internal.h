@@ -91,6 +91,16 @@ cudaError_t d2q9_pass(int precision, int pass, const void *params, const PassArg
 // one time step of every grid of a batch (strip width 128 or 64)
 cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
                             const BatchTile *tiles, int ntiles, int parity, cudaStream_t st);
+// nsteps time steps of every grid of a batch in one cooperative launch, one
+// resident CTA per tile (ntiles must not exceed the resident capacity:
+// d2q9_batch_persist_ctas_per_sm x SMs).  nbr: per tile PERSIST_NBMAX + 1
+// ints, the count of the tiles its stencil reaches, then their indices.
+// flags: ntiles ints (zeroed here); err: a device int set on a wait timeout.
+constexpr int PERSIST_NBMAX = 16;
+cudaError_t d2q9_batch_persist(int precision, int width, const BatchCase *cases, int ncases,
+                               const BatchTile *tiles, const int *nbr, int ntiles, int parity,
+                               int nsteps, int *flags, int *err, cudaStream_t st);
+int d2q9_batch_persist_ctas_per_sm(int precision, int width);
 cudaError_t d2q9_init(int precision, const void *params, const double *phi0, double *mu_tmp,
                       void *f, void *g, void *S, cudaStream_t st);
 cudaError_t d2q9_get_state(int precision, int nx, int ny, const void *f, const void *g,

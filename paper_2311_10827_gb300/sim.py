@@ -196,6 +196,15 @@ class Batch:
     def set_shape(self, width, rows):
         capi.check(capi.lbm_batch_set_shape(self._h, width, rows), "lbm_batch_set_shape")
 
+    def set_persistent(self, on=True):
+        """Multi-step launches (lbm_batch_set_persistent): one cooperative
+        launch per step(n) call, tiles synchronised with their neighbours."""
+        capi.check(capi.lbm_batch_set_persistent(self._h, int(on)), "lbm_batch_set_persistent")
+
+    def persistent(self, read_timeout=False):
+        """(on, timed_out) of lbm_batch_persistent."""
+        return capi.lbm_batch_persistent(self._h, read_timeout)
+
     @property
     def handle(self):
         return self._h
