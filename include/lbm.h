@@ -330,7 +330,10 @@ int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
  * a timeout the tile sets an error word, fills its region of S with NaN (so
  * that diagnostics report non-finite fields) and stops; see
  * lbm_batch_persistent.  Tunes first if the batch is untuned.
- * on = 0 returns to per-step launches (CUDA-graph replay).
+ * on = 0 returns to per-step launches (CUDA-graph replay).  A later
+ * lbm_batch_set_shape or lbm_batch_tune whose tiles do not fit the GPU at
+ * once runs per-step launches until a shape fits again (lbm_batch_persistent
+ * reports which is in use).  Single-step calls always launch once per step.
  * Errors: INVALID_ARG (NULL, or on = 1 with a shape whose tiles do not fit
  * the GPU at once), CUDA. */
 int lbm_batch_set_persistent(lbm_batch *b, int on);
