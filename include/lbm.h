@@ -327,9 +327,9 @@ int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
  * per-step launches.  It needs every tile of the current shape resident at
  * once (tiles <= resident CTAs per SM x SMs), so it suits batches whose
  * tiles fill about one wave.  A wait is bounded (about 2 s of SM clock). On
- * a timeout the tile sets an error word, fills its region of S with NaN (so
- * that diagnostics report non-finite fields) and stops; see
- * lbm_batch_persistent.  Tunes first if the batch is untuned.
+ * a timeout the tile sets an error word, fills its region of the rest
+ * population (both buffers) and of S with NaN (so that diagnostics report
+ * non-finite fields) and stops; see lbm_batch_persistent.  Tunes first if the batch is untuned.
  * on = 0 returns to per-step launches (CUDA-graph replay).  A later
  * lbm_batch_set_shape or lbm_batch_tune whose tiles do not fit the GPU at
  * once runs per-step launches until a shape fits again (lbm_batch_persistent
@@ -343,6 +343,18 @@ int lbm_batch_set_persistent(lbm_batch *b, int on);
  * neighbour tile.  Reading timed_out synchronises the device.
  * Errors: INVALID_ARG, CUDA. */
 int lbm_batch_persistent(const lbm_batch *b, int *on, int *timed_out);
+
+/* Fault injection for tests of the multi-step launch's bounded waits: make
+ * tile `tile` of the current shape wait, before every step after the first,
+ * on a counter that nothing sets.  The next multi-step launch then takes
+ * about 2 s to end.  The stalled tile gives up after its limit and sets the
+ * error word that lbm_batch_persistent reports.  The tiles waiting on it,
+ * directly or through others, see the error word and stop.  The state is
+ * left with NaN in the stalled tile's rest population and S.  The injection lasts until the tiles
+ * are rebuilt (lbm_batch_set_shape, lbm_batch_tune).
+ * Errors: INVALID_ARG (NULL, tile out of range, multi-step launches not in
+ * use), CUDA. */
+int lbm_batch_debug_stall(lbm_batch *b, int tile);
 
 /* Release the batch and all its contexts (synchronises first).  NULL-safe. */
 void lbm_batch_destroy(lbm_batch *b);

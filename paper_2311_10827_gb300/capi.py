@@ -33,7 +33,8 @@ EXPORTS = ("lbm_params_default", "lbm_create", "lbm_init_phi", "lbm_step", "lbm_
            "lbm_batch_case", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_shape",
            "lbm_batch_destroy", "lbm_batch_set_shape", "lbm_adjoint_create", "lbm_adjoint_forward",
            "lbm_adjoint_backward", "lbm_adjoint_destroy", "lbm_state_bytes",
-           "lbm_create_with_buffers", "lbm_batch_set_persistent", "lbm_batch_persistent")
+           "lbm_create_with_buffers", "lbm_batch_set_persistent", "lbm_batch_persistent",
+           "lbm_batch_debug_stall")
 
 
 class lbm_grid(ctypes.Structure):
@@ -116,6 +117,7 @@ def lib(path: str | None = None):
                                   ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_set_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.lbm_batch_set_persistent.argtypes = [vp, ctypes.c_int]
+    L.lbm_batch_debug_stall.argtypes = [vp, ctypes.c_int]
     L.lbm_batch_persistent.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
@@ -324,6 +326,10 @@ def lbm_batch_persistent(b, read_timeout=False):
     on, to = ctypes.c_int(), ctypes.c_int()
     check(lib().lbm_batch_persistent(b, ctypes.byref(on), ctypes.byref(to) if read_timeout else None))
     return bool(on.value), (bool(to.value) if read_timeout else None)
+
+
+def lbm_batch_debug_stall(b, tile):
+    return lib().lbm_batch_debug_stall(b, int(tile))
 
 
 def lbm_batch_destroy(b):

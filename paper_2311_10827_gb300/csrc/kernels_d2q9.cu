@@ -626,8 +626,9 @@ constexpr long long PERSIST_WAIT_CYCLES = 4000000000LL;
 // The FP32 shift of the source buffer is the stored one at step 0 and the
 // target after it (what step 0 wrote with); the caller records the final
 // buffer's shift.  A wait that runs past PERSIST_WAIT_CYCLES sets *err,
-// fills the tile's S with NaN (so the diagnostics report non-finite fields)
-// and ends the CTA; tiles waiting on it then time out too.
+// fills the tile's rest population (both buffers) and S with NaN (so the
+// diagnostics report non-finite fields) and ends the CTA; tiles waiting on
+// it see *err and end too.
 template <typename T, int TX>
 __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS_STATE, TX>::ctas))
     d2q9_batch_persist_kernel(const BatchCase *__restrict__ cases, const BatchTile *__restrict__ tiles,
@@ -665,11 +666,18 @@ __global__ void __launch_bounds__(TX *TYB, (Occ<T, PASS_STATE, TX>::ctas))
             }
             __syncthreads();
             if (s_abort) {
+                // the tile's state is invalid: NaN in its rest population of
+                // both buffers (so phi, whichever buffer is current) and in S
                 T *S = static_cast<T *>(c.S);
+                T *f0 = static_cast<T *>(c.f[0]), *f1 = static_cast<T *>(c.f[1]);
                 const int x = t.x0 + threadIdx.x;
                 if (x < P.nx)
-                    for (int y = t.y0 + (int)threadIdx.y; y < t.yend; y += TYB)
-                        S[(size_t)y * P.nx + x] = T(NAN);
+                    for (int y = t.y0 + (int)threadIdx.y; y < t.yend; y += TYB) {
+                        const size_t n = (size_t)y * P.nx + x;
+                        S[n] = T(NAN);
+                        f0[n] = T(NAN);
+                        f1[n] = T(NAN);
+                    }
                 return;
             }
         }
@@ -849,7 +857,8 @@ cudaError_t launch_persist_t(const BatchCase *cases, int ncases, const BatchTile
                              const int *nbr, int ntiles, int parity, int nsteps, int *flags,
                              int *err, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)ntiles * sizeof(int), st);
+    // the tiles' counters and the spare one that nothing sets (fault-injection tests)
+    cudaError_t e = cudaMemsetAsync(flags, 0, ((size_t)ntiles + 1) * sizeof(int), st);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&cases, (void *)&tiles, (void *)&nbr, (void *)&parity,
                     (void *)&nsteps, (void *)&flags, (void *)&err};

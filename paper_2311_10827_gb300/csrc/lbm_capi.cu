@@ -1006,7 +1006,7 @@ struct lbm_batch {
     int persist;     // requested
     int persist_ok;  // the current tiles fit the GPU at once and have neighbour lists
     int *d_nbr;      // per tile: count, then up to PERSIST_NBMAX neighbour tiles
-    int *d_flags;    // per tile: steps completed in the current launch
+    int *d_flags;    // per tile: steps completed in the current launch; one spare (never set)
     int *d_err;      // set by a wait that timed out
     int persist_cap; // tiles d_nbr and d_flags hold
 };
@@ -1106,7 +1106,7 @@ int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int 
         b->d_flags = nullptr;
         b->persist_cap = 0;
         if (cudaMalloc((void **)&b->d_nbr, (size_t)count * stride * sizeof(int)) != cudaSuccess ||
-            cudaMalloc((void **)&b->d_flags, (size_t)count * sizeof(int)) != cudaSuccess) {
+            cudaMalloc((void **)&b->d_flags, ((size_t)count + 1) * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             free(nb);
             return LBM_ERR_OOM;
@@ -1439,6 +1439,19 @@ int lbm_batch_persistent(const lbm_batch *b, int *on, int *timed_out)
             return LBM_ERR_CUDA;
         *timed_out = v;
     }
+    return LBM_OK;
+}
+
+int lbm_batch_debug_stall(lbm_batch *b, int tile)
+{
+    if (!b || tile < 0 || tile >= b->ntiles || !b->persist || !b->persist_ok)
+        return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    // one neighbour: the spare counter after the tiles' own (index ntiles)
+    const int rec[2] = {1, b->ntiles};
+    if (cudaMemcpy(b->d_nbr + (size_t)tile * (PERSIST_NBMAX + 1), rec, sizeof rec,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return LBM_ERR_CUDA;
     return LBM_OK;
 }
 

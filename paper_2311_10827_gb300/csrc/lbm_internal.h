@@ -95,7 +95,9 @@ cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
 // resident CTA per tile (ntiles must not exceed the resident capacity:
 // d2q9_batch_persist_ctas_per_sm x SMs).  nbr: per tile PERSIST_NBMAX + 1
 // ints, the count of the tiles its stencil reaches, then their indices.
-// flags: ntiles ints (zeroed here); err: a device int set on a wait timeout.
+// flags: ntiles + 1 ints, zeroed here (the last is a spare that nothing
+// sets: a neighbour index of ntiles stalls a tile, for fault-injection
+// tests); err: a device int set on a wait timeout.
 constexpr int PERSIST_NBMAX = 16;
 cudaError_t d2q9_batch_persist(int precision, int width, const BatchCase *cases, int ncases,
                                const BatchTile *tiles, const int *nbr, int ntiles, int parity,

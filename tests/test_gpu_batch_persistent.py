@@ -94,3 +94,42 @@ def test_set_persistent_rejects_shapes_that_do_not_fit(gpu):
         assert b.persistent()[0] is False
     finally:
         b.close()
+
+
+def test_stalled_tile_times_out_without_hanging(gpu):
+    """Fault injection: tile 0 waits on a counter that nothing sets.  The
+    launch must end by itself after the bounded wait (about 2 s of SM clock),
+    report the timeout, and leave non-finite fields that the diagnostics flag;
+    the GPU stays usable (a fresh batch then steps normally)."""
+    import time
+
+    from paper_2311_10827_gb300 import capi
+    cases = [((256, 128), dict(BASE, rho_l=10.0))] * 2
+    phi = wl.droplet(256, 128, 30.0, 4.0)
+    b = gpu.Batch(cases, precision="fp32")
+    try:
+        for i in range(len(b)):
+            b.case(i).init_phi(phi)
+        b.set_shape(128, 16)
+        b.set_persistent(True)
+        capi.check(capi.lbm_batch_debug_stall(b.handle, 0))
+        t = time.perf_counter()
+        b.step(4)
+        on, timed_out = b.persistent(read_timeout=True)
+        dt = time.perf_counter() - t
+        assert timed_out is True
+        assert 0.5 < dt < 30.0, dt
+        assert b.case(0).diagnostics()["nonfinite"]
+    finally:
+        b.close()
+    fresh = gpu.Batch(cases, precision="fp32")
+    try:
+        for i in range(len(fresh)):
+            fresh.case(i).init_phi(phi)
+        fresh.set_shape(128, 16)
+        fresh.set_persistent(True)
+        fresh.step(4)
+        assert fresh.persistent(read_timeout=True)[1] is False
+        assert not fresh.case(0).diagnostics()["nonfinite"]
+    finally:
+        fresh.close()
