@@ -315,13 +315,14 @@ def cpu_baseline_adjoint(budget_s=12.0, n=128, steps=40):
 def adjoint_bytes_per_node(esz):
     """Algorithmic bytes per node update of the differentiated run: the
     recorded forward step, the segment recomputation (which also writes the
-    five moments), adj_local, adj_mu and adj_phi (own-node values only;
+    five moments), adj_local and adj_mu_phi (own-node values only;
     checkpoint copies, 2 % of the bytes at K = 100, are not counted)."""
     lo = 1 if esz == 4 else 0              # FP32 rest-pair low word
     fwd = (18 + lo) * 2 * esz + 2 * esz    # f, g (+ lo) read and written, S
     rec = fwd + 5 * esz                    # + phi, mu, p, ux, uy written
     local = (18 + lo + 5 + 10 + 9 + 1) * esz + 25 * esz
-    return fwd + rec + local + 4 * esz + 6 * esz
+    mu_phi = 7 * esz + esz                 # lambda_mu, lambda_grad_mu, phi, lambda_phi, lambda_grad_phi; lpt
+    return fwd + rec + local + mu_phi
 
 
 def run_reference(args, rank, world, budget_s=90.0, est_mlups=2.0):
@@ -897,7 +898,7 @@ def run_adjoint(args, rank, world, local_rank):
                      "peak_source": f"{src} copy bandwidth (hbm_gbs)",
                      "algorithmic_bytes_per_node": bpn, "device_s": dev_s,
                      "kernel": "whole gradient (recorded forward, segment recomputation with "
-                               "moments, adj_local + adj_mu + adj_phi per reverse step); one "
+                               "moments, adj_local + adj_mu_phi per reverse step); one "
                                "step's data (2 x 21 MB) fits the 129 MB L2"},
         "e2e": {"value": nodes * nsteps * world / e2e_s / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": 2 * 8 * nodes / nsteps,
@@ -914,9 +915,9 @@ def run_adjoint(args, rank, world, local_rank):
         "clocks": clk.summary(t_start, t_end),
         # per gradient: initial condition (2), nsteps recorded steps, the
         # final phi (1), the seed, nsteps recomputation passes (one
-        # moments-only per segment among them), 3 reverse kernels per step,
+        # moments-only per segment among them), 2 reverse kernels per step,
         # the initial-condition reverse (2)
-        "gpu_launches": 5 * nsteps + 6,
+        "gpu_launches": 4 * nsteps + 6,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_adjoint()

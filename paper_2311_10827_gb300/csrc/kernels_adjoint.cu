@@ -20,10 +20,11 @@
 //      collisions and of the moments, leaving the adjoint of g and S_prev,
 //      the direct part of the adjoint of f, and the local adjoints of phi,
 //      mu, grad(phi), grad(mu);
-//   3. adj_mu: the transpose of the gradient stencil maps the grad(mu)
-//      adjoint onto mu;
-//   4. adj_phi: mu = psi'(phi) - kappa lap(phi) and phi = sum_i f_i are
-//      reversed (the Laplacian is symmetric, the gradient antisymmetric).
+//   3. adj_mu_phi: the transpose of the gradient stencil maps the grad(mu)
+//      adjoint onto mu (on a tile and its halo in shared memory), then
+//      mu = psi'(phi) - kappa lap(phi) and phi = sum_i f_i are reversed
+//      (the Laplacian is symmetric, the gradient antisymmetric).  adj_phi
+//      does the last part alone for the initial condition.
 #include <float.h>
 #include <math.h>
 
@@ -258,15 +259,6 @@ __device__ __forceinline__ R lap_at(const AdjGeom &g, const V *v, int x, int y)
     return s;
 }
 
-template <typename R>
-__global__ void adj_mu(AdjGeom geo, const R *__restrict__ lmu, const R *__restrict__ lgmu,
-                       R *__restrict__ lmu_tot)
-{
-    const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= geo.N) return;
-    const int x = n % geo.nx, y = n / geo.nx;
-    lmu_tot[n] = lmu[n] + gradT_at(geo, lgmu, x, y);
-}
 
 // lambda_phi total (the part of lambda_f common to every direction, lpt_out);
 // dL/dkappa, dL/dbeta
@@ -289,6 +281,49 @@ __global__ void adj_phi(const StepParams<R> P, AdjGeom geo, const V *__restrict_
         db = lm * R(4) * a * b * c;
         if (lpt_out) lpt_out[n] = l;
         if (lphi_out) lphi_out[n] = (double)l;
+    }
+    block_add(dk, dpar + 0);
+    block_add(db, dpar + 1);
+}
+
+// The mu and phi parts of a reverse step in one pass.  The block owns a 32 x 8
+// tile (256 threads) and first forms lambda_mu_tot = lambda_mu + G^T
+// lambda_grad_mu on the tile and a 1-node halo in shared memory (the halo
+// recomputed by each block), then the phi adjoint of adj_phi from it.
+constexpr int AMX = 32, AMY = 8, AHX = AMX + 2, AHY = AMY + 2;
+template <typename R>
+__global__ void __launch_bounds__(AMX *AMY)
+    adj_mu_phi(const StepParams<R> P, AdjGeom geo, const R *__restrict__ phi,
+               const R *__restrict__ lphi, const R *__restrict__ lgphi, const R *__restrict__ lmu,
+               const R *__restrict__ lgmu, R *__restrict__ lpt_out, double *dpar)
+{
+    __shared__ R smu[AHX * AHY];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * AMX, y0 = blockIdx.y * AMY;
+    for (int q = tid; q < AHX * AHY; q += AMX * AMY) {
+        // any grid size: a full modulo for the (at most 2) halo coordinates
+        int xx = (x0 - 1 + q % AHX) % geo.nx, yy = (y0 - 1 + q / AHX) % geo.ny;
+        xx += xx < 0 ? geo.nx : 0;
+        yy += yy < 0 ? geo.ny : 0;
+        smu[q] = lmu[(unsigned)yy * geo.nx + xx] + gradT_at(geo, lgmu, xx, yy);
+    }
+    __syncthreads();
+    const int x = x0 + tid % AMX, y = y0 + tid / AMX;
+    R dk = R(0), db = R(0);
+    if (x < geo.nx && y < geo.ny) {
+        const unsigned n = (unsigned)y * geo.nx + x;
+        const int c = (tid / AMX + 1) * AHX + tid % AMX + 1;
+        const R ph = phi[n], lm = smu[c];
+        const R a = ph - P.phil, b = ph - P.phiv, cc = ph - P.phibar;
+        const R d2psi = R(4) * P.beta * (b * cc + a * cc + a * b);
+        // symmetric Laplacian of lambda_mu_tot from the tile
+        R lap = R(0);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) lap += R(2.0 * wa(i) / CS2A) * (smu[c + cya(i) * AHX + cxa(i)] - lm);
+        const R l = lphi[n] + gradT_at(geo, lgphi, x, y) + d2psi * lm - P.kappa * lap;
+        dk = lm * (-lap_at<R>(geo, phi, x, y));
+        db = lm * R(4) * a * b * cc;
+        lpt_out[n] = l;
     }
     block_add(dk, dpar + 0);
     block_add(db, dpar + 1);
@@ -336,14 +371,13 @@ void adj_step_t(const StepParams<R> &P, AdjGeom geo, const R *f, const R *g, con
                 cudaStream_t st)
 {
     const unsigned N = geo.N;
-    R *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N, *lgmu = work + 4 * (size_t)N,
-      *lmu_tot = work + 6 * (size_t)N;
+    R *lphi = work, *lmu = work + N, *lgphi = work + 2 * (size_t)N, *lgmu = work + 4 * (size_t)N;
     const unsigned nb = (N + 255) / 256;
     adj_local<R><<<nb, 256, 0, st>>>(P, geo, f, g, phi, mu, p, u, lf_in, lpt, lg_in, lS_in,
                                      lf_out, lg_out, lS_out, lphi, lmu, lgphi, lgmu, dpar);
-    adj_mu<R><<<nb, 256, 0, st>>>(geo, lmu, lgmu, lmu_tot);
     // lpt is read (gathered) by adj_local above and rewritten here
-    adj_phi<R, R><<<nb, 256, 0, st>>>(P, geo, phi, lphi, lgphi, lmu_tot, lpt, nullptr, dpar);
+    const dim3 tiles((geo.nx + AMX - 1) / AMX, (geo.ny + AMY - 1) / AMY);
+    adj_mu_phi<R><<<tiles, AMX * AMY, 0, st>>>(P, geo, phi, lphi, lgphi, lmu, lgmu, lpt, dpar);
 }
 
 template <typename R>

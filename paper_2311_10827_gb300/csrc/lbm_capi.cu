@@ -1481,7 +1481,7 @@ struct lbm_adjoint {
     void *lf[2], *lg[2], *lS[2];  // adjoint fields at the adjoint precision
     void *lpt;                    // the adjoint of f common to all directions [N]
     double *macro;      // N doubles: device staging of dL/dphi0 for a host destination
-    void *work;         // 7N adjoint values (at least N doubles)
+    void *work;         // 6N adjoint values (at least N doubles)
     double *dpar;       // 3
 };
 
@@ -1546,7 +1546,7 @@ int lbm_adjoint_create(lbm_ctx *ctx, int checkpoint_every, int max_steps, lbm_ad
               cudaMalloc((void **)&a->seg, (size_t)checkpoint_every * a->slot) == cudaSuccess &&
               cudaMalloc((void **)&a->phi0, N * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&a->macro, N * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&a->work, 7 * N * a->rsz) == cudaSuccess &&
+              cudaMalloc(&a->work, 6 * N * a->rsz) == cudaSuccess &&
               cudaMalloc(&a->lpt, N * a->rsz) == cudaSuccess &&
               cudaMalloc((void **)&a->dpar, 3 * sizeof(double)) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b)
@@ -1594,7 +1594,7 @@ int lbm_adjoint_backward(lbm_adjoint *a, const double *dL_dphi, int on_device, d
     const size_t N = (size_t)ctx->N;
     const int nx = ctx->grid.nx, ny = ctx->grid.ny;
     // the seed: dL/dphi of the final state into the adjoint of every f_i
-    double *seed = (double *)a->work;  // 7 N adjoint values hold N doubles
+    double *seed = (double *)a->work;  // 6 N adjoint values hold N doubles
     CK(cudaMemcpyAsync(seed, dL_dphi, N * sizeof(double),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     int cb = 0;
