@@ -135,7 +135,7 @@ def test_fp64_phi_budget_on_gpu(gpu, oracle_mod):
 @pytest.mark.parametrize("precision,nx", [("fp64", 160), ("fp32", 160), ("fp32", 256)])
 def test_graph_and_plain_steps_identical(gpu, precision, nx):
     """lbm_step(n) (CUDA graph of 32 steps) equals n single steps bit for bit
-    (nx = 256 takes the TMA-staged FP32 kernel)."""
+    (nx = 256: full 128-column strips; nx = 160: a ragged last strip)."""
     a = gpu.Simulation((nx, 70), precision=precision, **PRM)
     b = gpu.Simulation((nx, 70), precision=precision, **PRM)
     phi0 = wl.droplet(nx, 70, 20.0, 4.0)
@@ -271,7 +271,7 @@ def test_nonfinite_is_reported(gpu, precision):
 
 
 def test_fp32_fused_diagnostics_close_to_on_demand(gpu):
-    """The TMA-staged step's fused diagnostics agree with the on-demand pass."""
+    """The FP32 step's fused diagnostics agree with the on-demand pass."""
     a = gpu.Simulation((256, 64), precision="fp32", diag_every=5, **PRM)
     b = gpu.Simulation((256, 64), precision="fp32", **PRM)
     phi0 = wl.droplet(256, 64, 15.0, 4.0)
@@ -302,7 +302,7 @@ def test_call_order_and_arguments(gpu):
 @pytest.mark.parametrize("shape", [(192, 96), (256, 96), (128, 77)])
 def test_fp32_against_oracle(gpu, oracle_mod, shape):
     """FP32 path vs the FP64 oracle on a droplet, 2000 steps (widths that are
-    multiples of 128 take the TMA-staged kernel)."""
+    multiples of 128 fill every 128-column strip; 192 leaves a ragged one)."""
     s = gpu.Simulation(shape, precision="fp32", **PRM)
     o = oracle_mod.Oracle(shape, **PRM)
     phi0 = wl.droplet(shape[0], shape[1], 24.0, 4.0)
