@@ -279,7 +279,8 @@ int lbm_debug_poke(lbm_ctx *ctx, int field, int i, long long n, double value);
  * Many independent periodic D2Q9 grids, each with its own size and problem
  * parameters (all at one precision), advance together: every time step is a
  * single kernel launch over a flat table of tiles that covers all grids, long
- * runs replay a CUDA graph of such launches, and the tile shape (strip width
+ * runs replay a CUDA graph of such launches (or run as one cooperative launch
+ * per call: lbm_batch_set_persistent), and the tile shape (strip width
  * 64 or 128 columns, rows per tile) is chosen by an autotuner that times
  * candidate shapes on the batch's own state.  Each grid is also an ordinary
  * context (lbm_batch_case) for initialisation, moments, diagnostics, state
@@ -322,14 +323,14 @@ int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
  * runs as ONE cooperative launch in which every tile keeps its CTA for all n
  * steps.  After each step a tile publishes a per-tile step counter, and before
  * the next it waits only for the tiles its stencil reaches (3 nodes) to reach
- * the same step.  Tiles therefore drift apart instead of starting and ending
- * every step together.  The results are the same, bit for bit, as those of
- * per-step launches.  It needs every tile of the current shape resident at
- * once (tiles <= resident CTAs per SM x SMs), so it suits batches whose
- * tiles fill about one wave.  A wait is bounded (about 2 s of SM clock). On
- * a timeout the tile sets an error word, fills its region of the rest
- * population (both buffers) and of S with NaN (so that diagnostics report
- * non-finite fields) and stops; see lbm_batch_persistent.  Tunes first if the batch is untuned.
+ * the same step: there is no grid-wide barrier and no launch per step.  The
+ * results are the same, bit for bit, as those of per-step launches.  It
+ * needs every tile of the current shape resident at once (tiles <= resident
+ * CTAs per SM x SMs), so it suits batches whose tiles fill about one wave.
+ * A wait is bounded (about 2 s of SM clock).  On a timeout the tile sets an
+ * error word, fills its region of the rest population (both buffers) and of
+ * S with NaN (so that diagnostics report non-finite fields) and stops; see
+ * lbm_batch_persistent.  Tunes first if the batch is untuned.
  * on = 0 returns to per-step launches (CUDA-graph replay).  A later
  * lbm_batch_set_shape or lbm_batch_tune whose tiles do not fit the GPU at
  * once runs per-step launches until a shape fits again (lbm_batch_persistent
@@ -350,8 +351,8 @@ int lbm_batch_persistent(const lbm_batch *b, int *on, int *timed_out);
  * about 2 s to end.  The stalled tile gives up after its limit and sets the
  * error word that lbm_batch_persistent reports.  The tiles waiting on it,
  * directly or through others, see the error word and stop.  The state is
- * left with NaN in the stalled tile's rest population and S.  The injection lasts until the tiles
- * are rebuilt (lbm_batch_set_shape, lbm_batch_tune).
+ * left with NaN in the stalled tile's rest population and S.  The injection
+ * lasts until the tiles are rebuilt (lbm_batch_set_shape, lbm_batch_tune).
  * Errors: INVALID_ARG (NULL, tile out of range, multi-step launches not in
  * use), CUDA. */
 int lbm_batch_debug_stall(lbm_batch *b, int tile);
