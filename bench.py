@@ -93,10 +93,16 @@ def measured_peaks():
 
 
 def kernel_hash():
+    """First 16 hex digits of the sha256 of the kernel sources with comments
+    and blank lines removed: a traffic record belongs to the code it was
+    taken on, whatever happens to the comments since."""
+    import re
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(l.rstrip() for l in text.split("\n") if l.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -620,8 +620,7 @@ constexpr long long PERSIST_WAIT_CYCLES = 4000000000LL;
 // every tile whose region its stencil reaches (nbr: count, then indices) has
 // published k + 1 (acquire).  Neighbours are then at most one step apart, so
 // a tile never reads a buffer a neighbour is still writing or writes one a
-// neighbour is still reading; no grid-wide barrier is needed, and tiles drift
-// apart instead of starting and ending every step together.  Populations
+// neighbour is still reading, and no grid-wide barrier is needed.  Populations
 // other tiles write in this launch are read through L2 (no read-only path).
 // The FP32 shift of the source buffer is the stored one at step 0 and the
 // target after it (what step 0 wrote with); the caller records the final

@@ -56,3 +56,15 @@ def test_committed_traffic_records_match_the_kernel_source():
         assert bench.ncu_traffic(mode) is not None, (mode, "re-capture the DRAM traffic")
         # the recorded bytes are close to the algorithmic 2 x 1024^2 x 160 B per step
         assert 0.8 < bench.ncu_traffic(mode) / (2 * 1024 * 1024 * 160) < 1.05
+
+
+def test_kernel_hash_follows_code_not_comments(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ("k.cu",))
+    src.write_text("// a step\nint f(int x) { return x + 1; }  // plus one\n")
+    h = bench.kernel_hash()
+    src.write_text("/* the step,\n   reworded */\n\nint f(int x) { return x + 1; }\n")
+    assert bench.kernel_hash() == h
+    src.write_text("// a step\nint f(int x) { return x + 2; }  // plus one\n")
+    assert bench.kernel_hash() != h
