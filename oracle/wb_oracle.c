@@ -54,6 +54,14 @@
 
 #define WBO_QMAX 19
 
+/* Coefficient of u.grad(rho) in the pressure recovery below Eq. GGi: the
+ * paper's dt/2.  The oracle always uses dt/2; the tests rebuild it with
+ * other values, on the CPU, only to show that their pins of this term fail
+ * for a dropped, doubled or sign-flipped term. */
+#ifndef WBO_P_UGR
+#define WBO_P_UGR 0.5
+#endif
+
 /* ------------------------------------------------------------------ lattice */
 
 typedef struct {
@@ -463,7 +471,7 @@ static void compute_macros(wbo_sim *s)
             ugr += u[a] * grho[a];
             ugp += u[a] * s->gphi[a * N + n];
         }
-        s->p[n] = CS2 / (1.0 - L->w[0]) * (sg + 0.5 * ugr + rho * s_node(L, 0, u));
+        s->p[n] = CS2 / (1.0 - L->w[0]) * (sg + WBO_P_UGR * ugr + rho * s_node(L, 0, u));
         s->rho[n] = rho;
         for (int a = 0; a < 3; ++a) s->u[a * N + n] = u[a];
         s->S[n] = ugp;                                       /* S = u.grad(phi) */
@@ -765,8 +773,8 @@ static void adjoint_step(wbo_sim *s, double *lf, double *lg, double *lS, double 
             const double k = CS2 / (1.0 - L->w[0]);
             for (int i = 1; i < Q; ++i) lg_new[i * N + x] += k * lp;
             for (int a = 0; a < D; ++a) {
-                lu[a] += k * lp * (0.5 * grho[a] - rho * L->w[0] * u[a] / CS2);
-                lgr[a] += k * lp * 0.5 * u[a];
+                lu[a] += k * lp * (WBO_P_UGR * grho[a] - rho * L->w[0] * u[a] / CS2);
+                lgr[a] += k * lp * WBO_P_UGR * u[a];
             }
             lrho += k * lp * (-L->w[0] * uu / (2 * CS2));
         }

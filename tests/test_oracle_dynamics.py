@@ -245,3 +245,76 @@ def test_brute_force_exact_rational(oracle_mod):
     assert np.abs(go - ge).max() < 1e-14 * max(1.0, np.abs(ge).max())
     assert np.abs(So - Se).max() < 1e-14
     assert np.abs(ge).max() > 1e-4 and np.abs(Se).max() > 1e-4
+
+
+def _translating_slab(O, U, steps, ny=64, ratio=10.0):
+    """A flat slab (Eq. flatinitial, interfaces normal to y, density ratio
+    `ratio`, tau_g = 1 in both phases) relaxed at rest for 3000 steps, then
+    given the uniform velocity (0, U): g = g^eq(p, rho(phi), U) from the
+    relaxed pressure, S_prev = U.grad(phi).  Returns (displacement of the
+    slab / (U t), max |u_y - U| / U, pressure range, the largest
+    cs2/(1 - w0) |u.grad(rho)| / 2 of the final state)."""
+    prm = dict(W=4.0, M=0.1, alpha=1.0, sigma=1e-3, rho_l=ratio, rho_v=1.0,
+               nu_l=1.0 / 6.0, nu_v=1.0 / 6.0)
+    o = O.Oracle((2, ny), **prm)
+    o.init_phi(wl.flat_interface(2, ny, 4.0))
+    o.step(3000)
+    m = o.macros()
+    f, g, S = o.get_state()
+    gp = o.grad(m["phi"])
+    for y in range(ny):
+        for x in range(2):
+            rho = 1.0 + (ratio - 1.0) * m["phi"][y, x]
+            g[:, y, x] = O.node_geq(m["p"][y, x], rho, (0.0, U))
+            S[y, x] = U * gp[1, y, x]
+    o.set_state(f, g, S, 0)
+
+    def centroid(phi):  # periodic: phase of the first Fourier mode of the profile
+        z = (phi[:, 0] * np.exp(2j * np.pi * np.arange(ny) / ny)).sum()
+        return np.angle(z) / (2 * np.pi) * ny
+
+    c0 = centroid(m["phi"])
+    o.step(steps)
+    m = o.macros()
+    disp = (centroid(m["phi"]) - c0 + 0.5 * ny) % ny - 0.5 * ny
+    uy = m["u"][1][:, 0]
+    p = m["p"][:, 0]
+    grho = (ratio - 1.0) * o.grad(m["phi"])[1][:, 0]
+    term = (1.0 / 3.0) / (1.0 - 4.0 / 9.0) * 0.5 * np.abs(uy * grho).max()
+    return disp / (U * steps), np.abs(uy - U).max() / U, p.max() - p.min(), term
+
+
+def test_translating_slab_pins_pressure_recovery(oracle_mod):
+    """Galilean invariance of the macroscopic equations the scheme recovers
+    (Section 2: incompressible Navier-Stokes with the surface force, and the
+    Cahn-Hilliard equation with convection): a flat equilibrium interface
+    moving with a uniform velocity U normal to it is an exact solution with
+    u = U and uniform p.  Only the u.grad(rho)/2 term of the pressure
+    recovery below Eq. GGi carries the density jump into p when u crosses
+    the interfaces (it is zero in every other pin: static states, rho_l =
+    rho_v, or flows along the interfaces).  At U = 1e-3 and density ratio 10
+    the slab must move at U within 3%, u stay within 20% of U, and p stay
+    uniform to a third of that term's largest value."""
+    U = 1e-3
+    ratio, dev_u, p_range, term = _translating_slab(oracle_mod, U, 2000)
+    assert abs(ratio - 1.0) < 0.03, ratio
+    assert dev_u < 0.2, dev_u
+    assert p_range < term / 3.0, (p_range, term)
+
+
+@pytest.mark.parametrize("coef", ["0.0", "1.0", "-0.5"])
+def test_translating_slab_fails_with_a_wrong_pressure_term(oracle_mod, coef, tmp_path,
+                                                          monkeypatch):
+    """The pin above is sharp: the oracle rebuilt with the u.grad(rho) term
+    dropped, doubled or sign-flipped (the only change) fails it."""
+    import subprocess
+    so = str(tmp_path / "libwb_oracle_variant.so")
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", f"-DWBO_P_UGR={coef}",
+                    "-o", so, oracle_mod._SRC, "-lm"], check=True)
+    monkeypatch.setattr(oracle_mod, "_LIB", so)
+    monkeypatch.setattr(oracle_mod, "_lib", None)
+    monkeypatch.setattr(oracle_mod, "build", lambda force=False: so)
+    with np.errstate(all="ignore"):
+        ratio, dev_u, p_range, term = _translating_slab(oracle_mod, 1e-3, 2000)
+    ok = abs(ratio - 1.0) < 0.03 and dev_u < 0.2 and p_range < term / 3.0
+    assert not ok, (coef, ratio, dev_u, p_range, term)
