@@ -54,12 +54,15 @@ sys.path.insert(0, ROOT)
 
 NX = NY = 1024
 RATIOS = (10.0, 100.0)
-# bytes moved per node update: f, g read + write (4 Q s) and S read + write;
-# FP32 also moves the low word of the rest population pair (8 B)
-BYTES_PER_NODE = {"fp32": 160, "fp64": 304}
-# D3Q19: FP32 4 Q 4 + 8 (rest pair low word) + 8 (S); FP64 4 Q 8 + 16; 16-bit
-# offsets: 4 Q 2 + 2 x 24 (six FP32 macros read and written) + 8 (S)
-BYTES_PER_NODE_3D = {"fp32": 320, "fp64": 624, "f16off": 208, "bf16off": 208}
+# algorithmic bytes per node update: f and g each read once and written once
+# (4 Q s) and S read + written (8 B FP32, 16 B FP64).  Anything else the
+# kernels move (the FP32 rest population's low word, halo re-reads, phi work
+# fields) is overhead and shows in the measured `traffic`.
+BYTES_PER_NODE = {"fp32": 4 * 9 * 4 + 8, "fp64": 4 * 9 * 8 + 16}
+# D3Q19 likewise; 16-bit offsets: 4 Q 2 + 2 x 24 (six FP32 macros read and
+# written) + 8 (S)
+BYTES_PER_NODE_3D = {"fp32": 4 * 19 * 4 + 8, "fp64": 4 * 19 * 8 + 16,
+                     "f16off": 4 * 19 * 2 + 2 * 24 + 8, "bf16off": 4 * 19 * 2 + 2 * 24 + 8}
 DTYPE = {"fp32": "f32", "fp64": "f64", "f16off": "f32 (f16 offset storage)",
          "bf16off": "f32 (bf16 offset storage)"}
 KERNEL_SOURCES = ("paper_2311_10827_gb300/csrc/kernels_d2q9.cu",)
@@ -369,6 +372,26 @@ def run_reference(args, rank, world, budget_s=90.0, est_mlups=2.0):
     print(json.dumps(line), flush=True)
 
 
+# The stream is held by a short sleep kernel (torch's own, about 1 ms)
+# between the synchronisation before a timed region and the region's first
+# event, so that the host has enqueued the region's work by the time the
+# first event fires: the events then time the device work of the steps, not
+# the host's enqueue latency.  The sleep is outside the events.
+GATE_CYCLES = 2_000_000
+
+
+def gate():
+    import torch
+    torch.cuda._sleep(GATE_CYCLES)
+
+
+def diag_cadence(args):
+    """Diagnostics cadence of the timed runs: every --diag-every steps, and at
+    least once in every timed region of --steps steps (any run of k
+    consecutive steps holds exactly one multiple of k)."""
+    return max(1, min(args.diag_every, args.steps))
+
+
 def run_native(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -384,10 +407,12 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     prec = args.precision
-    de = args.diag_every
+    de = diag_cadence(args)
+    K = args.steps
     n = args.size or NX  # grid edge (1024: the headline; 4096: the out-of-L2 point)
     R = wl.DROPLET_1024["R"] * n / NX
     cases = [((n, n), params(r)) for r in RATIOS]
+    nodes = n * n * len(cases)
 
     def barrier():
         if world > 1:
@@ -397,14 +422,8 @@ def run_native(args, rank, world, local_rank):
     def max_over_ranks(x):
         return max_over_ranks_dist(x, world, dev)
 
-    def chunks(k):
-        out, left = [], k
-        while left > 0:
-            out.append(min(de, left))
-            left -= out[-1]
-        return out
-
-    # ---- device-resident timing: one batched launch per step over both grids
+    # ---- device-resident timing: the whole step (both grids) per launch,
+    # diagnostics fused into the step that starts at each multiple of `de`
     batch = Batch(cases, precision=prec, stream=stream.cuda_stream)
     phi_d = torch.tensor(phi0(n), dtype=torch.float64, device=dev)
     for i in range(len(batch)):
@@ -414,47 +433,44 @@ def run_native(args, rank, world, local_rank):
         batch.set_shape(width, rows)
     else:
         width, rows = batch.tune()
-    multi = False
-    if not args.per_step:
-        # one cooperative launch per chunk of steps when every tile of the
-        # tuned shape fits the GPU at once (bit-identical to per-step launches)
-        try:
-            batch.set_persistent(True)
-            multi = True
-        except capi.LbmError:
-            pass
-    plan = chunks(args.steps)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in plan]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    multi = not args.per_step
+    if multi:
+        batch.set_persistent(True)
+    batch.set_diag_every(de)
+    # The timed region (exactly K steps between two device synchronisations)
+    # is repeated until about --min-time seconds of timed work, so that the
+    # clock sampler sees it; `value` uses the mean over the repetitions.
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps_s = []
     with ClockSampler(local_rank) as clk:
         batch.step(args.warmup)
         barrier()
         t_wall = time.perf_counter()
         t_start = time.time()
-        t0.record(stream)
-        for (a, b), m in zip(ev, plan):
-            a.record(stream)
-            batch.step(m)
-            b.record(stream)
-            for i in range(len(batch)):  # FP64 diagnostics of both grids (a10)
-                rc, d = capi.lbm_diagnostics(batch.case(i).handle)
-                capi.check(rc)
-                if d.nonfinite:
-                    raise RuntimeError("non-finite fields in the timed run")
-        t1.record(stream)
-        barrier()
+        while True:
+            barrier()
+            gate()
+            ev0.record(stream)
+            batch.step(K)
+            ev1.record(stream)
+            barrier()
+            reps_s.append(max_over_ranks(ev0.elapsed_time(ev1) / 1e3))
+            if len(reps_s) >= args.repeat_min and (
+                    sum(reps_s) >= args.min_time or len(reps_s) >= args.repeat_max):
+                break
         t_wall = time.perf_counter() - t_wall
         t_end = time.time()
-    total_s = max_over_ranks(t0.elapsed_time(t1) / 1e3)
-    kernel_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps  # per step
-    nodes = n * n * len(cases)
-    value = nodes * args.steps * world / total_s / 1e6
+    recs = batch.last_diagnostics()
+    if any(r["nonfinite"] for r in recs):
+        raise RuntimeError("non-finite fields in the timed run")
+    total_s = statistics.fmean(reps_s)
+    value = nodes * K * world / total_s / 1e6
     ntiles = batch.shape()[2]
     batch.close()
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: phi0 of both grids
+    # from pinned host memory, K steps with the fused diagnostics records read
+    # on the host, final moments of both grids to pinned host memory
     hphi = torch.tensor(phi0(n), dtype=torch.float64).pin_memory()
     hphi_np = hphi.numpy()
     out_t = [{k: torch.empty(m * n * n, dtype=torch.float64).pin_memory()
@@ -464,26 +480,28 @@ def run_native(args, rank, world, local_rank):
     eb.set_shape(width, rows)  # the tile shape tuned above (tuning is one-time setup)
     if multi:
         eb.set_persistent(True)
-    barrier()
-    t_e = time.perf_counter()
-    for i in range(len(eb)):
-        capi.check(capi.lbm_init_phi(eb.case(i).handle, hphi_np, 0))
-    n_diag_reads = 0
-    for m in plan:
-        capi.check(capi.lbm_batch_step(eb.handle, m))
+    eb.set_diag_every(de)
+    e2e_runs = []
+    for _ in range(args.e2e_runs):
+        barrier()
+        t_e = time.perf_counter()
         for i in range(len(eb)):
-            rc, d = capi.lbm_diagnostics(eb.case(i).handle)  # device -> host read
-            capi.check(rc)
-            n_diag_reads += 1
-    for i, o in enumerate(outs):
-        capi.check(capi.lbm_moments(eb.case(i).handle, o["phi"], o["p"], o["u"], o["mu"], 0))
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t_e)
+            capi.check(capi.lbm_init_phi(eb.case(i).handle, hphi_np, 0))
+        capi.check(capi.lbm_batch_step(eb.handle, K))
+        rc, erecs = capi.lbm_batch_last_diagnostics(eb.handle, len(eb))  # device -> host
+        capi.check(rc)
+        for i, o in enumerate(outs):
+            capi.check(capi.lbm_moments(eb.case(i).handle, o["phi"], o["p"], o["u"], o["mu"], 0))
+        barrier()
+        e2e_runs.append(max_over_ranks(time.perf_counter() - t_e))
+        if any(r.nonfinite for r in erecs):
+            raise RuntimeError("non-finite fields in the end-to-end run")
     eb.close()
-    e2e_value = nodes * args.steps * world / e2e_s / 1e6
-    diag_bytes = ctypes_sizeof_diag()
-    h2d = n * n * 8 * len(cases) / args.steps
-    d2h = (n_diag_reads * diag_bytes + 5 * n * n * 8 * len(cases)) / args.steps
+    e2e_s = statistics.fmean(e2e_runs)
+    e2e_value = nodes * K * world / e2e_s / 1e6
+    h2d = n * n * 8 * len(cases) / K
+    n_diag = (K + de - 1) // de
+    d2h = (n_diag * len(cases) * DIAG_RECORD_BYTES + 5 * n * n * 8 * len(cases)) / K
 
     if rank != 0:
         return
@@ -495,8 +513,8 @@ def run_native(args, rank, world, local_rank):
         ref.set_shape(width, rows)  # no tuning
         for i in range(len(ref)):
             ref.case(i).init_phi(phi_d)
-        ref.step(args.steps)
-        accuracy = {"steps": args.steps, "max_u_fp32": 0.0, "max_u_fp64": 0.0,
+        ref.step(K)
+        accuracy = {"steps": K, "max_u_fp32": 0.0, "max_u_fp64": 0.0,
                     "max_abs_u_diff_vs_fp64": 0.0, "max_abs_phi_diff_vs_fp64": 0.0,
                     "reference": "FP64 GPU path (parity with the FP64 oracle at 1e-12), same "
                                  "phi0 and steps, both density ratios"}
@@ -514,48 +532,57 @@ def run_native(args, rank, world, local_rank):
         ref.close()
     peaks, src = measured_peaks()
     bpn = BYTES_PER_NODE[prec]
-    achieved = bpn * nodes / kernel_s / 1e9
+    achieved = bpn * nodes * K / total_s / 1e9
     traffic = (ncu_traffic("multi_step" if multi else "per_step")
                if prec == "fp32" and n == NX else None)
+    launches = (launches_multi_step(args.warmup, K, de) if multi else K + (K + de - 1) // de)
     line = {
         "metric": "MLUPS (fused f+g step)", "value": value, "unit": "MLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+        "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_s / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
         "data": "synthetic",
         "config": {"workload": f"2D stationary droplet {n}x{n} periodic, R={R:g}, W=4, "
                                "sigma=1e-3, M=0.05, nu_l/nu_v=10, rho_l/rho_v=10 and 100 "
-                               "(one step = both grids, one batched launch)",
+                               "(one step = both grids)",
                    "lattice": "D2Q9", "nodes_per_step": nodes, "diag_every": de,
+                   "diagnostics": "FP64 diagnostics of both grids fused into the step that "
+                                  "starts at each multiple of diag_every (one per timed region), "
+                                  "reduced on the device, records read on the host after the "
+                                  "timed regions",
                    "tile": {"width": width, "rows": rows, "ctas": ntiles},
-                   "launch": ("one cooperative launch per chunk of steps, each tile "
-                              "synchronised with its neighbours" if multi
-                              else "one launch per step, CUDA-graph replay"),
+                   "launch": ("one cooperative launch per timed region: a queue of "
+                              "(step, tile) pairs, each tile synchronised with its neighbours"
+                              if multi else "one launch per step, CUDA-graph replay"),
+                   "timed_regions": {"count": len(reps_s), "steps_each": K,
+                                     "start": "behind a ~1 ms sleep kernel issued after the "
+                                              "synchronisation, so the events time the device "
+                                              "work, not the host's enqueue",
+                                     "ms_min": min(reps_s) * 1e3,
+                                     "ms_median": statistics.median(reps_s) * 1e3,
+                                     "ms_max": max(reps_s) * 1e3,
+                                     "value_is": "mean over the regions"},
                    "l2": f"inputs larger than L2: 2 x {80 * n * n / 1e6:.0f} MB read per step, "
                          "back to back",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": traffic, "peak_source": f"{src} copy bandwidth (hbm_gbs)",
-                     "algorithmic_bytes_per_node": bpn, "kernel_ms": kernel_s * 1e3,
-                     "kernel": ("d2q9_batch_persist_kernel (both grids, diag_every steps per "
-                                "launch; per-step time and traffic)" if multi
-                                else "d2q9_batch_kernel (both grids per launch)")},
+                     "algorithmic_bytes_per_node": bpn, "step_ms": total_s / K * 1e3,
+                     "kernel": ("d2q9_batch_persist_kernel (both grids, one launch per timed "
+                                "region; time of the whole region, per step; traffic per step)"
+                                if multi else "d2q9_batch_kernel (both grids per launch)")},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
-                "how": "wall clock through the C ABI: lbm_init_phi from pinned host phi0, "
-                       "lbm_batch_step (tile shape from the tuning of the device-timed run, set "
-                       "before the region) in chunks of diag_every steps each followed "
-                       "by lbm_diagnostics (device-to-host read) of both grids, final "
-                       "lbm_moments of both grids to host"},
+                "d2h_bytes_per_step": d2h, "runs": len(e2e_runs),
+                "how": "wall clock through the C ABI, mean of the runs: lbm_init_phi of both "
+                       "grids from pinned host phi0, lbm_batch_step of K steps with the fused "
+                       "diagnostics (tile shape from the device-timed run's tuning, set "
+                       "before the region), lbm_batch_last_diagnostics (the records, read on "
+                       "the host), final lbm_moments of both grids to pinned host memory"},
         "accuracy": accuracy,
-        # one step kernel per step; per chunk and grid the diagnostics pass,
-        # its reduction and (FP32) the equilibrium-shift update
-        # multi-step: per chunk the cooperative launch and the shift record
-        "gpu_launches": (2 * len(plan) if multi else args.steps)
-        + len(plan) * len(cases) * (3 if prec == "fp32" else 2),
+        "gpu_launches": launches,
         "clocks": clk.summary(t_start, t_end),
-        "wall_s_timed_region": t_wall,
+        "wall_s_timed_regions": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -563,11 +590,59 @@ def run_native(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+DIAG_RECORD_BYTES = 64  # one FP64 record per grid: 8 doubles on the device
+
+
+def launches_multi_step(t0, k, de):
+    """Kernel launches of one multi-step lbm_batch_step(k) call starting at
+    time t0 with diagnostics every de steps: the launch is split so that it
+    holds at most one diagnostics step (the library's rule)."""
+    count, t, left = 0, t0, k
+    while left > 0:
+        m = left
+        d = (t + de - 1) // de * de
+        if d < t + m and d + de < t + m:
+            m = d + de - t
+        count += 1
+        t += m
+        left -= m
+    return count
+
+
+def partition_cases(sizes, world):
+    """Split independent cases over `world` ranks, balanced by node count:
+    largest first, each to the rank with the fewest nodes so far (ties to the
+    lowest rank).  Returns one sorted list of case indices per rank; every
+    case lands on exactly one rank."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda j: (-sizes[j], j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def combine_ranks(local_nodes, local_s, world, device):
+    """Whole-job figures of a partitioned run: the node updates of all ranks
+    over the slowest rank's time (the job ends when its last rank does)."""
+    if world <= 1:
+        return local_nodes, local_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_nodes)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item()), max_over_ranks_dist(local_s, world, device)
+
+
 def run_ensemble(args, rank, world, local_rank):
     """The batched ensemble: 256 stationary droplets, N x N grids with N drawn
     from U{64..512}, R = U(0.15, 0.35) N, rho_l/rho_v = U(1, 100) (seeds 0..255,
-    workloads.ensemble_case), W = 4, other parameters of the 1024^2 droplet;
-    one batched launch per step."""
+    workloads.ensemble_case), W = 4, other parameters of the 1024^2 droplet.
+    With N ranks the cases are partitioned across them (balanced by node
+    count, no exchange: the cases are independent); each rank advances its
+    share as one batch, one multi-step launch per call (the tiles walked as a
+    queue), diagnostics fused every --diag-every steps."""
     import torch
 
     from paper_2311_10827_gb300 import build as B
@@ -578,30 +653,43 @@ def run_ensemble(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     base = wl.physical(wl.DROPLET_1024)
+    allc = [wl.ensemble_case(seed) for seed in range(256)]
+    mine = partition_cases([c["n"] * c["n"] for c in allc], world)[rank]
     cases, phis = [], []
-    for seed in range(256):
-        c = wl.ensemble_case(seed)
+    for i in mine:
+        c = allc[i]
         prm = dict(base, rho_l=c["rho_ratio"] * base["rho_v"])
         cases.append(((c["n"], c["n"]), prm))
         phis.append(wl.droplet(c["n"], c["n"], c["R"], base["W"]))
+    de = diag_cadence(args)
     b = Batch(cases, precision=args.precision, stream=stream.cuda_stream)
     for i, phi in enumerate(phis):
         b.case(i).init_phi(phi)
     width, rows = b.tune()
+    multi = not args.per_step
+    if multi:
+        b.set_persistent(True)
+    b.set_diag_every(de)
     ctas = b.shape()[2]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         b.step(args.warmup)
         torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         t_start = time.time()
+        gate()
         e0.record(stream)
         b.step(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
         t_end = time.time()
-    dt = max_over_ranks_dist(e0.elapsed_time(e1) / 1e3, world, dev)
+    if any(r["nonfinite"] for r in b.last_diagnostics()):
+        raise RuntimeError("non-finite fields in the timed run")
+    local_nodes = sum(sh[0] * sh[1] for sh, _ in cases)
+    nodes, dt = combine_ranks(local_nodes, e0.elapsed_time(e1) / 1e3, world, dev)
     b.close()
-    nodes = sum(sh[0] * sh[1] for sh, _ in cases)
 
     # end to end through the C ABI with host buffers: every grid's phi0 from
     # pinned host memory, the same steps, every grid's final phi to host
@@ -612,6 +700,9 @@ def run_ensemble(args, rank, world, local_rank):
     hout = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for p in phis]
     eb = Batch(cases, precision=args.precision, stream=stream.cuda_stream)
     eb.set_shape(width, rows)  # the tuned shape (tuning is one-time setup)
+    if multi:
+        eb.set_persistent(True)
+    eb.set_diag_every(de)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for i in range(len(eb)):
@@ -619,38 +710,51 @@ def run_ensemble(args, rank, world, local_rank):
     capi.check(capi.lbm_batch_step(eb.handle, args.steps))
     for i in range(len(eb)):
         capi.check(capi.lbm_moments(eb.case(i).handle, hout[i].numpy(), None, None, None, 0))
+    rc, erecs = capi.lbm_batch_last_diagnostics(eb.handle, len(eb))
+    capi.check(rc)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks_dist(time.perf_counter() - t, world, dev)
+    _, e2e_s = combine_ranks(local_nodes, time.perf_counter() - t, world, dev)
     eb.close()
-    if not all(np.isfinite(o.numpy()).all() for o in hout):
+    if not all(np.isfinite(o.numpy()).all() for o in hout) or any(r.nonfinite for r in erecs):
         raise RuntimeError("non-finite phi in the end-to-end run")
     peaks, src = measured_peaks()
     bpn = BYTES_PER_NODE[args.precision]
     if rank == 0:
-        v = nodes * args.steps * world / dt / 1e6
+        v = nodes * args.steps / dt / 1e6
+        n_diag = (args.steps + de - 1) // de
         line = {
             "metric": "MLUPS (fused f+g step)", "value": v, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "batched ensemble: 256 stationary 2D droplets, grids "
                                    "64^2..512^2, seeds 0..255", "nodes_per_step": nodes,
+                       "partition": f"cases split over {world} rank(s) by node count, no "
+                                    "exchange (rank 0 holds "
+                                    f"{len(mine)} cases, {local_nodes} nodes)",
                        "tile": {"width": width, "rows": rows, "ctas": ctas},
+                       "launch": ("one cooperative launch per call: a queue of (step, tile) "
+                                  "pairs over every grid's tiles" if multi
+                                  else "one launch per step, CUDA-graph replay"),
+                       "diag_every": de,
                        "l2": "inputs larger than L2: 27.5M nodes, 2.2 GB read per step"},
             "roofline": {"bound": "hbm", "achieved": bpn * v * 1e6 / 1e9 / world,
                          "peak": peaks["hbm_gbs"],
                          "frac": bpn * v * 1e6 / 1e9 / world / peaks["hbm_gbs"], "unit": "GB/s",
                          "traffic": None, "peak_source": f"{src} copy bandwidth (hbm_gbs)",
                          "algorithmic_bytes_per_node": bpn,
-                         "kernel": "d2q9_batch_kernel (all 256 grids per launch)"},
-            "e2e": {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+                         "kernel": ("d2q9_batch_persist_kernel" if multi else "d2q9_batch_kernel")
+                                   + " (all of the rank's grids per launch)"},
+            "e2e": {"value": nodes * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": 8 * nodes / args.steps,
-                    "d2h_bytes_per_step": 8 * nodes / args.steps,
+                    "d2h_bytes_per_step": (8 * nodes + n_diag * 256 * DIAG_RECORD_BYTES)
+                                          / args.steps,
                     "how": "wall clock through the C ABI: lbm_init_phi of every grid from "
                            "pinned host phi0, lbm_batch_step (tuned shape set before the "
-                           "region), lbm_moments of every grid's phi to pinned host memory"},
-            # one batched launch per step (graph replay), no diagnostics in the region
-            "gpu_launches": args.steps,
+                           "region), lbm_moments of every grid's phi to pinned host memory, "
+                           "the fused diagnostics records"},
+            "gpu_launches": (launches_multi_step(args.warmup, args.steps, de) if multi
+                             else args.steps + n_diag),
             "clocks": clk.summary(t_start, t_end),
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -706,6 +810,7 @@ def run_coalescence3d(args, rank, world, local_rank):
         d_first = sim.diagnostics()
         torch.cuda.synchronize()
         t_start = time.time()
+        gate()
         t0.record(stream)
         for (a, b), m in zip(ev, plan):
             a.record(stream)
@@ -957,6 +1062,12 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64", "f16off", "bf16off"], default="fp32",
                     help="f16off / bf16off: 16-bit offset storage (coalescence3d only)")
     ap.add_argument("--diag-every", type=int, default=100)
+    ap.add_argument("--min-time", type=float, default=1.0,
+                    help="droplet1024: repeat the timed region of --steps steps until about "
+                         "this many seconds of timed work (clock samples)")
+    ap.add_argument("--repeat-min", type=int, default=3)
+    ap.add_argument("--repeat-max", type=int, default=2000)
+    ap.add_argument("--e2e-runs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP64 comparison run after the timed region (profiling)")

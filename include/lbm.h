@@ -174,7 +174,8 @@ int lbm_create_with_buffers(const lbm_grid *grid, int lattice, const lbm_params 
 
 /* Set the initial condition from an order-parameter field phi[N] (FP64):
  * f = f^eq(phi, mu(phi)) (Eq. H_i), g = 0 (p = 0, u = 0), S_prev = 0, time 0.
- * on_device = 0: host array (copied, the call returns once it is read);
+ * on_device = 0: host array (uploaded through the context's own state
+ * buffers, no allocation; the call returns once it is read);
  * on_device = 1: device array.  Errors: INVALID_ARG, CUDA. */
 int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device);
 
@@ -303,8 +304,34 @@ int lbm_batch_case(lbm_batch *b, int c, lbm_ctx **ctx);
 
 /* Advance every grid by n >= 0 steps (asynchronous).  All grids must be
  * initialised and at the same time step.  The first call runs the autotuner
- * unless lbm_batch_tune was called.  Errors: STATE, INVALID_ARG, CUDA. */
+ * unless lbm_batch_tune was called.  With diagnostics on
+ * (lbm_batch_set_diag_every), the steps whose starting time is a multiple of
+ * the cadence carry them.  Errors: STATE, INVALID_ARG, CUDA; TIMEOUT after a
+ * multi-step launch gave up waiting (returned by every later call until
+ * lbm_batch_set_shape or lbm_batch_tune rebuilds the tiles); NONFINITE (once)
+ * when the last diagnostics saw NaN/Inf in a grid. */
 int lbm_batch_step(lbm_batch *b, int n);
+
+/* Fused diagnostics of every grid (a10): with k > 0, every batch step that
+ * starts at a time t that is a multiple of k also computes the FP64
+ * diagnostics of each grid's state at t (as lbm_step does with
+ * params.diag_every) from the same pass: one partial record per tile, a
+ * per-grid reduction on the device in a fixed order, and the records written
+ * to pinned host memory with no host synchronisation.  FP32 grids then move
+ * their equilibrium shift to the middle of the mu range, as lbm_diagnostics
+ * does (taking effect with the next launch).  k = 0 turns them off (the
+ * default).  The records are read with lbm_batch_last_diagnostics.  Errors:
+ * INVALID_ARG (NULL, k < 0). */
+int lbm_batch_set_diag_every(lbm_batch *b, int k);
+
+/* The records of the most recent fused diagnostics step, one per grid
+ * (out[ncases]; out[c].step = that step's time).  Waits for that step only.
+ * Errors: INVALID_ARG, STATE (no diagnostics step has run), CUDA. */
+int lbm_batch_last_diagnostics(lbm_batch *b, lbm_diag *out);
+
+/* Wait for all work issued on the batch's stream; returns a pending error
+ * (TIMEOUT, NONFINITE) as lbm_batch_step does.  Errors: INVALID_ARG, CUDA. */
+int lbm_batch_sync(lbm_batch *b);
 
 /* Time every candidate tile shape on the current state (the state is left
  * unchanged: candidates write only to scratch) and keep the fastest; report
@@ -320,28 +347,30 @@ int lbm_batch_shape(const lbm_batch *b, int *width, int *rows, int *ntiles);
 int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
 
 /* Multi-step launches.  With on = 1, an lbm_batch_step call of n >= 2 steps
- * runs as ONE cooperative launch in which every tile keeps its CTA for all n
- * steps.  After each step a tile publishes a per-tile step counter, and before
- * the next it waits only for the tiles its stencil reaches (3 nodes) to reach
- * the same step: there is no grid-wide barrier and no launch per step.  The
- * results are the same, bit for bit, as those of per-step launches.  It
- * needs every tile of the current shape resident at once (tiles <= resident
- * CTAs per SM x SMs), so it suits batches whose tiles fill about one wave.
- * A wait is bounded (about 2 s of SM clock).  On a timeout the tile sets an
- * error word, fills its region of the rest population (both buffers) and of
- * S with NaN (so that diagnostics report non-finite fields) and stops; see
- * lbm_batch_persistent.  Tunes first if the batch is untuned.
- * on = 0 returns to per-step launches (CUDA-graph replay).  A later
- * lbm_batch_set_shape or lbm_batch_tune whose tiles do not fit the GPU at
- * once runs per-step launches until a shape fits again (lbm_batch_persistent
- * reports which is in use).  Single-step calls always launch once per step.
- * Errors: INVALID_ARG (NULL, or on = 1 with a shape whose tiles do not fit
- * the GPU at once), CUDA. */
+ * runs as one cooperative launch (split where needed so that each launch
+ * carries at most one diagnostics step).  The launch holds every resident
+ * CTA slot of the GPU and works through a queue of (step, tile) pairs in
+ * order: before a tile's next step, its CTA waits only until the tile and
+ * the tiles its stencil reaches (3 nodes) have finished the previous step,
+ * each of them publishing a per-tile step counter.  There is no grid-wide
+ * barrier and no launch per step, any number of tiles fits (a batch of many
+ * grids walks its tile list every step), and tiles of the next step start
+ * while the last ones of a step still run.  The results are the same, bit
+ * for bit, as those of per-step launches.  A wait is bounded (about 2 s of
+ * SM clock).  On a timeout the tile sets an error word, fills its region of
+ * the rest population (both buffers) and of S with NaN (so that diagnostics
+ * report non-finite fields) and stops; the launch then ends, lbm_batch_step
+ * returns LBM_ERR_TIMEOUT from then on, and lbm_batch_persistent reports it.
+ * Tunes first if the batch is untuned.  on = 0 returns to per-step launches
+ * (CUDA-graph replay).  Single-step calls always launch once per step.
+ * Errors: INVALID_ARG (NULL, or on = 1 with a shape whose tiles have more
+ * than 16 neighbour tiles), CUDA. */
 int lbm_batch_set_persistent(lbm_batch *b, int on);
 
 /* *on (optional): whether multi-step launches are in use.  *timed_out
  * (optional): whether a multi-step launch has timed out waiting for a
- * neighbour tile.  Reading timed_out synchronises the device.
+ * neighbour tile since the tiles were last built.  Reading timed_out
+ * synchronises the device.
  * Errors: INVALID_ARG, CUDA. */
 int lbm_batch_persistent(const lbm_batch *b, int *on, int *timed_out);
 

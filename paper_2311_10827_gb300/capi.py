@@ -34,7 +34,8 @@ EXPORTS = ("lbm_params_default", "lbm_create", "lbm_init_phi", "lbm_step", "lbm_
            "lbm_batch_destroy", "lbm_batch_set_shape", "lbm_adjoint_create", "lbm_adjoint_forward",
            "lbm_adjoint_backward", "lbm_adjoint_destroy", "lbm_state_bytes",
            "lbm_create_with_buffers", "lbm_batch_set_persistent", "lbm_batch_persistent",
-           "lbm_batch_debug_stall")
+           "lbm_batch_debug_stall", "lbm_batch_set_diag_every", "lbm_batch_last_diagnostics",
+           "lbm_batch_sync")
 
 
 class lbm_grid(ctypes.Structure):
@@ -119,6 +120,9 @@ def lib(path: str | None = None):
     L.lbm_batch_set_persistent.argtypes = [vp, ctypes.c_int]
     L.lbm_batch_debug_stall.argtypes = [vp, ctypes.c_int]
     L.lbm_batch_persistent.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_set_diag_every.argtypes = [vp, ctypes.c_int]
+    L.lbm_batch_last_diagnostics.argtypes = [vp, ctypes.POINTER(lbm_diag)]
+    L.lbm_batch_sync.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     L.lbm_adjoint_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
@@ -330,6 +334,21 @@ def lbm_batch_persistent(b, read_timeout=False):
 
 def lbm_batch_debug_stall(b, tile):
     return lib().lbm_batch_debug_stall(b, int(tile))
+
+
+def lbm_batch_set_diag_every(b, k):
+    return lib().lbm_batch_set_diag_every(b, int(k))
+
+
+def lbm_batch_last_diagnostics(b, ncases):
+    """(rc, [lbm_diag] * ncases)."""
+    out = (lbm_diag * int(ncases))()
+    rc = lib().lbm_batch_last_diagnostics(b, out)
+    return rc, list(out)
+
+
+def lbm_batch_sync(b):
+    return lib().lbm_batch_sync(b)
 
 
 def lbm_batch_destroy(b):

@@ -42,7 +42,7 @@ struct lbm_ctx {
     int codec;   // offset storage: OFFSET_F16 / OFFSET_BF16, else -1
     size_t fbytes, gbytes;  // bytes of one f / g state buffer
     float *scw;  // offset storage: target scales [2], then 2 words of scratch
-    float *eqs;  // FP32 equilibrium shift {buffer 0, buffer 1, target} (device)
+    float *eqs;  // FP32 equilibrium shift {buffer 0, buffer 1, target, next target} (device)
     int own_state;  // f[], g[] and S were allocated here (not by the caller)
     int recentre;  // lbm_diagnostics moves the FP32 equilibrium shift (not under an adjoint)
     int nsm;
@@ -94,62 +94,16 @@ int take_err(lbm_ctx *c)
     return e;
 }
 
-bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
-
 int validate(const lbm_grid *g, int lattice, const lbm_params *p)
 {
-    if (!g || !p) return LBM_ERR_INVALID_ARG;
-    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_ERR_INVALID_ARG;
-    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_ERR_INVALID_ARG;
-    if (lattice == LBM_D2Q9 && g->nz != 1) return LBM_ERR_INVALID_ARG;
-    // population offsets are 32-bit in the kernels (up to 20 arrays: the 19
-    // D3Q19 populations and the FP32 rest population's low word)
-    if ((long long)g->nx * g->ny * g->nz * 20 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
-    if (!finite_pos(p->W) || !isfinite(p->sigma) || p->sigma < 0.0) return LBM_ERR_INVALID_ARG;
-    if (!finite_pos(p->M)) return LBM_ERR_INVALID_ARG;
-    if (p->tau_f == 0.0) {
-        if (!finite_pos(p->alpha)) return LBM_ERR_INVALID_ARG;
-    } else if (!isfinite(p->tau_f) || p->tau_f <= 0.5) {
-        return LBM_ERR_INVALID_ARG;
-    }
-    if (!isfinite(p->phi_l) || !isfinite(p->phi_v) || p->phi_l == p->phi_v)
-        return LBM_ERR_INVALID_ARG;
-    if (!finite_pos(p->rho_l) || !finite_pos(p->rho_v)) return LBM_ERR_INVALID_ARG;
-    if (!finite_pos(p->nu_l) || !finite_pos(p->nu_v)) return LBM_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (!isfinite(p->body_force[a])) return LBM_ERR_INVALID_ARG;
-    if (p->precision != LBM_FP64 && p->precision != LBM_FP32 &&
-        p->precision != LBM_FP32_F16OFF && p->precision != LBM_FP32_BF16OFF)
-        return LBM_ERR_INVALID_ARG;
-    // 16-bit offset storage is built for the D3Q19 path
-    if ((p->precision == LBM_FP32_F16OFF || p->precision == LBM_FP32_BF16OFF) &&
-        lattice != LBM_D3Q19)
-        return LBM_ERR_INVALID_ARG;
-    if (p->diag_every < 0) return LBM_ERR_INVALID_ARG;
-    return LBM_OK;
+    return validate_problem(g, lattice, p);
 }
 
 template <typename T>
 void fill_params(StepParams<T> &P, const lbm_ctx *c)
 {
-    const lbm_params &p = c->prm;
-    const double dphi = p.phi_l - p.phi_v;
-    P.nx = c->grid.nx;
-    P.ny = c->grid.ny;
-    P.nz = c->grid.nz;
-    P.N = c->N;
-    P.kappa = (T)c->kappa;
-    P.beta = (T)c->beta;
-    P.phil = (T)p.phi_l;
-    P.phiv = (T)p.phi_v;
-    P.phibar = (T)(0.5 * (p.phi_l + p.phi_v));
-    P.alpha = (T)c->alpha;
-    P.inv_tauf = (T)(1.0 / c->tau_f);
-    P.rhov = (T)p.rho_v;
-    P.drho = (T)((p.rho_l - p.rho_v) / dphi);
-    P.nuv = (T)p.nu_v;
-    P.dnu = (T)((p.nu_l - p.nu_v) / dphi);
-    for (int a = 0; a < 3; ++a) P.G[a] = (T)p.body_force[a];
+    const Derived d = {c->kappa, c->beta, c->tau_f, c->alpha};
+    fill_step_params(P, c->grid, c->prm, d);
 }
 
 const void *params_ptr(const lbm_ctx *c)
@@ -244,10 +198,10 @@ const float OFFSET_INITIAL_SCALES[2] = {OFFSET_SCALE_FLOOR, OFFSET_SCALE_FLOOR};
 int set_eq_shift(lbm_ctx *ctx, float a)
 {
     if (a == 0.0f) {
-        CK(cudaMemsetAsync(ctx->eqs, 0, 3 * sizeof(float), ctx->stream));
+        CK(cudaMemsetAsync(ctx->eqs, 0, 4 * sizeof(float), ctx->stream));
         return LBM_OK;
     }
-    float v[3] = {a, a, a};
+    float v[4] = {a, a, a, a};
     CK(cudaMemcpyAsync(ctx->eqs, v, sizeof v, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // v is on the stack
     return LBM_OK;
@@ -450,17 +404,11 @@ int create_impl(const lbm_grid *grid, int lattice, const lbm_params *params, voi
     const size_t ssz = params->precision == LBM_FP64 ? 8 : 4;
     ctx->stream = (cudaStream_t)cuda_stream;
 
-    // Eqs. beta and suiface_tension solved for kappa and beta; Eq. mobility.
-    const double d2 = (params->phi_l - params->phi_v) * (params->phi_l - params->phi_v);
-    ctx->kappa = 3.0 * params->W * params->sigma / (2.0 * d2);
-    ctx->beta = 12.0 * params->sigma / (params->W * d2 * d2);
-    if (params->tau_f == 0.0) {
-        ctx->alpha = params->alpha;
-        ctx->tau_f = 0.5 + params->M / (CS2 * params->alpha);
-    } else {
-        ctx->tau_f = params->tau_f;
-        ctx->alpha = params->M / (CS2 * (params->tau_f - 0.5));
-    }
+    const Derived dp = derive_params(*params);
+    ctx->kappa = dp.kappa;
+    ctx->beta = dp.beta;
+    ctx->tau_f = dp.tau_f;
+    ctx->alpha = dp.alpha;
     fill_params(ctx->pd, ctx);
     fill_params(ctx->pf, ctx);
 
@@ -508,7 +456,7 @@ int create_impl(const lbm_grid *grid, int lattice, const lbm_params *params, voi
     dalloc((void **)&ctx->aux, N * sizeof(double));
     if (lattice == LBM_D3Q19) dalloc(&ctx->phiw, N * ssz);
     if (ctx->codec >= 0) dalloc((void **)&ctx->scw, 4 * sizeof(float));
-    dalloc((void **)&ctx->eqs, 3 * sizeof(float));
+    dalloc((void **)&ctx->eqs, 4 * sizeof(float));
     ctx->recentre = 1;
     dalloc((void **)&ctx->partials, (size_t)ctx->npart * sizeof(DiagPartial));
     dalloc((void **)&ctx->dres, 2 * sizeof(DiagPartial));
@@ -546,25 +494,16 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     const size_t N = (size_t)ctx->N;
     const double *src = phi;
-    double *tmp = nullptr;
     if (!on_device) {
-        CK(cudaMalloc((void **)&tmp, N * sizeof(double)));
-        cudaError_t e = cudaMemcpyAsync(tmp, phi, N * sizeof(double), cudaMemcpyHostToDevice,
-                                        ctx->stream);
-        if (e != cudaSuccess) {
-            cudaFree(tmp);
-            return fail_cuda(ctx, e);
-        }
-        src = tmp;
+        // staged through the other f buffer: the initial condition writes
+        // buffer 0 only, and an f buffer holds at least N doubles (>= 9 N
+        // 4-byte or 19 N 2-byte values, 256-byte aligned)
+        double *stage = static_cast<double *>(ctx->f[1]);
+        CK(cudaMemcpyAsync(stage, phi, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        src = stage;
     }
+    if (int rc = set_eq_shift(ctx, 0.0f)) return rc;
     cudaError_t e = cudaSuccess;
-    if (int rc = set_eq_shift(ctx, 0.0f)) {
-        if (tmp) {
-            cudaStreamSynchronize(ctx->stream);
-            cudaFree(tmp);
-        }
-        return rc;
-    }
     if (ctx->codec >= 0) {
         e = cudaMemcpyAsync(ctx->scw, OFFSET_INITIAL_SCALES, sizeof OFFSET_INITIAL_SCALES,
                             cudaMemcpyHostToDevice, ctx->stream);
@@ -578,11 +517,8 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
         e = d2q9_init(ctx->prm.precision, &ctx->pd, src, ctx->aux, ctx->f[0], ctx->g[0],
                       ctx->S, ctx->stream);
     }
-    if (tmp) {
-        cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
-        cudaFree(tmp);
-        if (e == cudaSuccess) e = e2;
-    }
+    // a host array is read until the upload completes: return after it
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
     CK(e);
     ctx->cur = 0;
     ctx->step = 0;
@@ -988,6 +924,14 @@ const char *lbm_strerror(int code)
 
 // ------------------------------------------------------------------ batches
 
+// Status of a batch in mapped pinned host memory (written by the device):
+// the timeout word, then one diagnostics record per grid.
+struct BatchStatus {
+    int err;  // a multi-step launch timed out
+    int pad[15];
+};
+DiagPartial *status_rec(BatchStatus *s) { return reinterpret_cast<DiagPartial *>(s + 1); }
+
 struct lbm_batch {
     int n;
     lbm_ctx **ctx;
@@ -997,18 +941,28 @@ struct lbm_batch {
     BatchCase *d_cases;       // S_out = S (real steps)
     BatchCase *d_cases_tune;  // S_out = scratch (tuning leaves the state unchanged)
     BatchTile *d_tiles;
+    int *d_tile0;             // ncases + 1: first tile of each grid
     int tiles_cap, ntiles;
     int width, rows, tuned;
     cudaGraphExec_t gexec;
     int gexec_valid;
-    int err;
-    // multi-step launches (one resident CTA per tile for the whole call)
+    int err;                  // sticky error of the batch (LBM_ERR_TIMEOUT until a reset)
+    // multi-step launches (a queue of (step, tile) pairs per cooperative launch)
     int persist;     // requested
-    int persist_ok;  // the current tiles fit the GPU at once and have neighbour lists
+    int persist_ok;  // the current tiles have neighbour lists
     int *d_nbr;      // per tile: count, then up to PERSIST_NBMAX neighbour tiles
-    int *d_flags;    // per tile: steps completed in the current launch; one spare (never set)
+    int *d_ctr;      // 4 counters, then per tile the steps completed; one spare (never set)
     int *d_err;      // set by a wait that timed out
-    int persist_cap; // tiles d_nbr and d_flags hold
+    int persist_cap; // tiles d_nbr and d_ctr hold
+    // fused diagnostics
+    int diag_every;          // 0: none; else every step starting at a multiple of it
+    DiagPartial *d_partials; // one per tile
+    int partials_cap;
+    BatchStatus *h_status;   // mapped pinned host memory: error word and per-grid records
+    BatchStatus *d_status;   // its device address
+    cudaEvent_t diag_ev;     // recorded after the launch that wrote the records
+    int diag_pending, has_last_diag;
+    long long last_diag_step;
 };
 
 namespace {
@@ -1018,12 +972,12 @@ constexpr int BATCH_GRAPH_STEPS = 32;
 void batch_free(lbm_batch *b)
 {
     if (b->gexec_valid) cudaGraphExecDestroy(b->gexec);
-    if (b->d_nbr) cudaFree(b->d_nbr);
-    if (b->d_flags) cudaFree(b->d_flags);
-    if (b->d_err) cudaFree(b->d_err);
-    if (b->d_cases) cudaFree(b->d_cases);
-    if (b->d_cases_tune) cudaFree(b->d_cases_tune);
-    if (b->d_tiles) cudaFree(b->d_tiles);
+    void *dev[] = {b->d_nbr, b->d_ctr, b->d_err, b->d_cases, b->d_cases_tune, b->d_tiles,
+                   b->d_tile0, b->d_partials};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->diag_ev) cudaEventDestroy(b->diag_ev);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->ctx) {
         for (int c = 0; c < b->n; ++c) lbm_destroy(b->ctx[c]);
@@ -1041,18 +995,30 @@ void batch_free(lbm_batch *b)
         }                                               \
     } while (0)
 
-// tiles of every grid: strips of `width` columns, row tiles of `rows` rows,
-// row-major per grid; odd row tiles march up
+// device buffers of at least `count` ints / records, reallocated on growth
+int grow(void **p, int *cap, int count, size_t elem)
+{
+    if (count <= *cap) return LBM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, (size_t)count * elem) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return LBM_ERR_OOM;
+    }
+    *cap = count;
+    return LBM_OK;
+}
+
 // Neighbour lists of the tiles for multi-step launches: for every tile the
 // other tiles of its grid whose region meets the tile's stencil reach (3
 // nodes: phi at radius 2 is summed from populations pulled at radius 1),
-// periodic.  Sets persist_ok when every tile fits the GPU at once and no list
-// is longer than PERSIST_NBMAX.
+// periodic.  Sets persist_ok unless a list is longer than PERSIST_NBMAX.
 int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int rows)
 {
     b->persist_ok = 0;
-    const int per_sm = d2q9_batch_persist_ctas_per_sm(b->precision == LBM_FP64 ? 0 : 1, width);
-    if (per_sm < 1 || count > per_sm * b->nsm || rows < 1) return LBM_OK;
+    if (rows < 1) return LBM_OK;
     constexpr int REACH = 3;
     const int stride = PERSIST_NBMAX + 1;
     int *nb = (int *)malloc((size_t)count * stride * sizeof(int));
@@ -1100,14 +1066,14 @@ int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int 
         return LBM_OK;
     }
     if (count > b->persist_cap) {
+        int cap_nbr = 0, cap_ctr = 0;
         if (b->d_nbr) cudaFree(b->d_nbr);
-        if (b->d_flags) cudaFree(b->d_flags);
+        if (b->d_ctr) cudaFree(b->d_ctr);
         b->d_nbr = nullptr;
-        b->d_flags = nullptr;
+        b->d_ctr = nullptr;
         b->persist_cap = 0;
-        if (cudaMalloc((void **)&b->d_nbr, (size_t)count * stride * sizeof(int)) != cudaSuccess ||
-            cudaMalloc((void **)&b->d_flags, ((size_t)count + 1) * sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
+        if (grow((void **)&b->d_nbr, &cap_nbr, count * stride, sizeof(int)) ||
+            grow((void **)&b->d_ctr, &cap_ctr, count + 5, sizeof(int))) {
             free(nb);
             return LBM_ERR_OOM;
         }
@@ -1124,6 +1090,8 @@ int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int 
     return LBM_OK;
 }
 
+// tiles of every grid: strips of `width` columns, row tiles of `rows` rows,
+// row-major per grid; odd row tiles march up
 int batch_build_tiles(lbm_batch *b, int width, int rows)
 {
     long long count = 0;
@@ -1133,11 +1101,17 @@ int batch_build_tiles(lbm_batch *b, int width, int rows)
     }
     if (count > (1LL << 30)) return LBM_ERR_INVALID_ARG;
     BatchTile *h = (BatchTile *)malloc((size_t)count * sizeof(BatchTile));
-    if (!h) return LBM_ERR_OOM;
+    int *t0 = (int *)malloc(((size_t)b->n + 1) * sizeof(int));
+    if (!h || !t0) {
+        free(h);
+        free(t0);
+        return LBM_ERR_OOM;
+    }
     long long k = 0;
     for (int c = 0; c < b->n; ++c) {
         const lbm_grid &g = b->ctx[c]->grid;
         const int ty = (g.ny + rows - 1) / rows;
+        t0[c] = (int)k;
         for (int r = 0; r < ty; ++r)
             for (int x0 = 0; x0 < g.nx; x0 += width) {
                 BatchTile t;
@@ -1149,25 +1123,21 @@ int batch_build_tiles(lbm_batch *b, int width, int rows)
                 h[k++] = t;
             }
     }
-    if (count > b->tiles_cap) {
-        if (b->d_tiles) cudaFree(b->d_tiles);
-        b->d_tiles = nullptr;
-        if (cudaMalloc((void **)&b->d_tiles, (size_t)count * sizeof(BatchTile)) != cudaSuccess) {
-            free(h);
-            b->tiles_cap = 0;
-            b->err = LBM_ERR_CUDA;
-            return LBM_ERR_OOM;
-        }
-        b->tiles_cap = (int)count;
-    }
-    cudaError_t e = cudaMemcpy(b->d_tiles, h, (size_t)count * sizeof(BatchTile), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        free(h);
+    t0[b->n] = (int)k;
+    int rc = grow((void **)&b->d_tiles, &b->tiles_cap, (int)count, sizeof(BatchTile));
+    if (rc == LBM_OK)
+        rc = grow((void **)&b->d_partials, &b->partials_cap, (int)count, sizeof(DiagPartial));
+    if (rc == LBM_OK &&
+        (cudaMemcpy(b->d_tiles, h, (size_t)count * sizeof(BatchTile), cudaMemcpyHostToDevice) !=
+             cudaSuccess ||
+         cudaMemcpy(b->d_tile0, t0, ((size_t)b->n + 1) * sizeof(int), cudaMemcpyHostToDevice) !=
+             cudaSuccess)) {
         b->err = LBM_ERR_CUDA;
-        return LBM_ERR_CUDA;
+        rc = LBM_ERR_CUDA;
     }
-    const int rc = batch_build_nbr(b, h, (int)count, width, rows);
+    if (rc == LBM_OK) rc = batch_build_nbr(b, h, (int)count, width, rows);
     free(h);
+    free(t0);
     if (rc) return rc;
     b->ntiles = (int)count;
     b->width = width;
@@ -1190,10 +1160,23 @@ int batch_ready(lbm_batch *b)
     return LBM_OK;
 }
 
-int batch_launch(lbm_batch *b, const BatchCase *cases, int parity, cudaStream_t st)
+int batch_launch(lbm_batch *b, const BatchCase *cases, int parity, cudaStream_t st,
+                 DiagPartial *partials = nullptr)
 {
-    BK(d2q9_batch_step(b->precision, b->width, cases, b->d_tiles, b->ntiles, parity, st));
+    BK(d2q9_batch_step(b->precision, b->width, cases, b->d_tiles, b->ntiles, parity, partials,
+                       st));
     return LBM_OK;
+}
+
+// tiles of every grid at strip width w and r rows per tile
+long long count_tiles(const lbm_batch *b, int w, int r)
+{
+    long long n = 0;
+    for (int c = 0; c < b->n; ++c) {
+        const lbm_grid &g = b->ctx[c]->grid;
+        n += (long long)((g.nx + w - 1) / w) * ((g.ny + r - 1) / r);
+    }
+    return n;
 }
 
 int batch_tune(lbm_batch *b)
@@ -1209,8 +1192,22 @@ int batch_tune(lbm_batch *b)
     int bw = 128, br = 16;
     int rc = LBM_OK;
     for (int wi = 0; wi < 2 && rc == LBM_OK; ++wi) {
-        for (int ri = 0; ri < NR && rc == LBM_OK; ++ri) {
-            rc = batch_build_tiles(b, widths[wi], rowsc[ri]);
+        // the listed row counts, and the shortest even one whose tiles fill
+        // one wave of resident CTAs (every SM then holds the same number)
+        int cand[NR + 1], nc = 0;
+        for (int ri = 0; ri < NR; ++ri) cand[nc++] = rowsc[ri];
+        const int per_sm = d2q9_batch_persist_ctas_per_sm(b->precision == LBM_FP64 ? 0 : 1,
+                                                          widths[wi]);
+        const long long slots = (long long)(per_sm > 0 ? per_sm : 4) * b->nsm;
+        for (int r = 2; r <= 256; r += 2)
+            if (count_tiles(b, widths[wi], r) <= slots) {
+                bool listed = false;
+                for (int ri = 0; ri < NR; ++ri) listed = listed || rowsc[ri] == r;
+                if (!listed) cand[nc++] = r;
+                break;
+            }
+        for (int ri = 0; ri < nc && rc == LBM_OK; ++ri) {
+            rc = batch_build_tiles(b, widths[wi], cand[ri]);
             if (rc) break;
             for (int k = 0; k < 2 && rc == LBM_OK; ++k)
                 rc = batch_launch(b, b->d_cases_tune, parity, b->stream);
@@ -1224,7 +1221,7 @@ int batch_tune(lbm_batch *b)
             if (rc == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
                 best = ms;
                 bw = widths[wi];
-                br = rowsc[ri];
+                br = cand[ri];
             }
         }
     }
@@ -1263,6 +1260,148 @@ void batch_advance(lbm_batch *b, int steps)
         b->ctx[c]->cur ^= (steps & 1);
         b->ctx[c]->step += steps;
     }
+}
+
+// the records of the last diagnostics launch, once it has completed (or at
+// once with wait): non-finite fields become the batch's pending error
+void batch_poll(lbm_batch *b, bool wait)
+{
+    volatile int *herr = &b->h_status->err;  // written by the device
+    if (*herr && b->err == LBM_OK) b->err = LBM_ERR_TIMEOUT;
+    if (!b->diag_pending) return;
+    const cudaError_t e = wait ? cudaEventSynchronize(b->diag_ev) : cudaEventQuery(b->diag_ev);
+    if (e == cudaErrorNotReady) return;
+    if (e != cudaSuccess) {
+        b->err = LBM_ERR_CUDA;
+        return;
+    }
+    b->diag_pending = 0;
+    if (*herr && b->err == LBM_OK) b->err = LBM_ERR_TIMEOUT;
+    for (int c = 0; c < b->n; ++c)
+        if (status_rec(b->h_status)[c].nonfinite != 0.0 && b->err == LBM_OK) b->err = LBM_ERR_NONFINITE;
+}
+
+// the batch's error, once: a timeout stays until the tiles are rebuilt
+int batch_take_err(lbm_batch *b)
+{
+    const int e = b->err;
+    if (e == LBM_ERR_NONFINITE) b->err = LBM_OK;
+    return e;
+}
+
+// first step >= t that carries diagnostics, or -1
+long long next_diag(const lbm_batch *b, long long t)
+{
+    if (b->diag_every <= 0) return -1;
+    const long long k = b->diag_every;
+    return (t + k - 1) / k * k;
+}
+
+// n steps as multi-step launches, each holding at most one diagnostics step
+int batch_run_persistent(lbm_batch *b, int n)
+{
+    const int prec = b->precision == LBM_FP64 ? 0 : 1;
+    const int cap = (int)((0x7fffffff - 1) / (b->ntiles > 0 ? b->ntiles : 1));
+    int left = n;
+    while (left > 0) {
+        const long long t = b->ctx[0]->step;
+        int m = left < cap ? left : cap;
+        const long long d = next_diag(b, t);
+        int diag_k = -1;
+        if (d >= 0 && d < t + m) {
+            diag_k = (int)(d - t);
+            const long long d2 = d + b->diag_every;  // the next one starts a new launch
+            if (d2 < t + m) m = (int)(d2 - t);
+        }
+        PersistArgs pa;
+        pa.cases = b->d_cases;
+        pa.tiles = b->d_tiles;
+        pa.nbr = b->d_nbr;
+        pa.tile0 = b->d_tile0;
+        pa.ntiles = b->ntiles;
+        pa.ncases = b->n;
+        pa.parity0 = b->ctx[0]->cur;
+        pa.nsteps = m;
+        pa.diag_k = diag_k;
+        pa.ctr = b->d_ctr;
+        pa.flags = b->d_ctr + 4;
+        pa.err = b->d_err;
+        pa.err_host = &b->d_status->err;
+        pa.partials = b->d_partials;
+        pa.records = status_rec(b->d_status);
+        const int per_sm = d2q9_batch_persist_ctas_per_sm(prec, b->width);
+        if (per_sm < 1) {
+            b->err = LBM_ERR_CUDA;
+            return LBM_ERR_CUDA;
+        }
+        // one CTA per tile when they all fit at once, else a queue over every slot
+        const long long pairs = (long long)m * b->ntiles, slots = (long long)per_sm * b->nsm;
+        const int nctas = b->ntiles <= slots ? b->ntiles : (int)(pairs < slots ? pairs : slots);
+        BK(d2q9_batch_persist(prec, b->width, pa, nctas, b->stream));
+        if (diag_k >= 0) {
+            BK(cudaEventRecord(b->diag_ev, b->stream));
+            b->diag_pending = 1;
+            b->has_last_diag = 1;
+            b->last_diag_step = t + diag_k;
+        }
+        batch_advance(b, m);
+        left -= m;
+    }
+    return LBM_OK;
+}
+
+// one step with diagnostics of its source state (per-step launches)
+int batch_diag_step(lbm_batch *b)
+{
+    const long long t = b->ctx[0]->step;
+    if (int rc = batch_launch(b, b->d_cases, b->ctx[0]->cur, b->stream, b->d_partials)) return rc;
+    BK(d2q9_batch_reduce(b->precision == LBM_FP64 ? 0 : 1, b->d_partials, b->d_tile0, b->d_cases,
+                         b->n, status_rec(b->d_status), b->stream));
+    BK(cudaEventRecord(b->diag_ev, b->stream));
+    b->diag_pending = 1;
+    b->has_last_diag = 1;
+    b->last_diag_step = t;
+    batch_advance(b, 1);
+    return LBM_OK;
+}
+
+// n plain steps as per-step launches (CUDA-graph replay of 32-step blocks)
+int batch_run_plain(lbm_batch *b, int n)
+{
+    int left = n;
+    if (left >= BATCH_GRAPH_STEPS) {
+        if (b->ctx[0]->cur == 1) {
+            if (int rc = batch_launch(b, b->d_cases, 1, b->stream)) return rc;
+            batch_advance(b, 1);
+            --left;
+        }
+        if (left >= BATCH_GRAPH_STEPS) {
+            if (int rc = batch_graph(b)) return rc;
+            const int reps = left / BATCH_GRAPH_STEPS;
+            for (int r = 0; r < reps; ++r) BK(cudaGraphLaunch(b->gexec, b->stream));
+            batch_advance(b, reps * BATCH_GRAPH_STEPS);
+            left -= reps * BATCH_GRAPH_STEPS;
+        }
+    }
+    for (; left > 0; --left) {
+        if (int rc = batch_launch(b, b->d_cases, b->ctx[0]->cur, b->stream)) return rc;
+        batch_advance(b, 1);
+    }
+    return LBM_OK;
+}
+
+// a rebuild of the tiles clears a timeout: the error words and the sticky error
+int batch_reset_timeout(lbm_batch *b)
+{
+    if (b->err != LBM_ERR_TIMEOUT && !*(volatile int *)&b->h_status->err) return LBM_OK;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+        cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
+        b->err = LBM_ERR_CUDA;
+        return LBM_ERR_CUDA;
+    }
+    b->h_status->err = 0;
+    if (b->err == LBM_ERR_TIMEOUT) b->err = LBM_OK;
+    return LBM_OK;
 }
 
 }  // namespace
@@ -1313,13 +1452,20 @@ int lbm_batch_create(int ncases, const lbm_grid *grids, const lbm_params *params
         h[c].S = x->S;
         h[c].S_out = x->S;
         h[c].eqs = x->eqs;
+        h[c].recentre = x->recentre;
     }
     const size_t bytes = (size_t)ncases * sizeof(BatchCase);
+    const size_t sbytes = sizeof(BatchStatus) + (size_t)ncases * sizeof(DiagPartial);
     bool ok = cudaMalloc((void **)&b->d_cases, bytes) == cudaSuccess &&
               cudaMalloc((void **)&b->d_cases_tune, bytes) == cudaSuccess &&
               cudaMemcpy(b->d_cases, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_tile0, ((size_t)ncases + 1) * sizeof(int)) == cudaSuccess &&
               cudaMalloc((void **)&b->d_err, sizeof(int)) == cudaSuccess &&
-              cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess;
+              cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess &&
+              cudaHostAlloc((void **)&b->h_status, sbytes, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&b->d_status, b->h_status, 0) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->diag_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) memset(b->h_status, 0, sbytes);
     for (int c = 0; c < ncases && ok; ++c) h[c].S_out = b->ctx[c]->aux;  // scratch for tuning
     ok = ok && cudaMemcpy(b->d_cases_tune, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1351,52 +1497,65 @@ int lbm_batch_case(lbm_batch *b, int c, lbm_ctx **ctx)
     return LBM_OK;
 }
 
-int lbm_batch_tune(lbm_batch *b, int *width, int *rows)
-{
-    if (!b) return LBM_ERR_INVALID_ARG;
-    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
-    if (int rc = batch_ready(b)) return rc;
-    if (int rc = batch_tune(b)) return rc;
-    if (width) *width = b->width;
-    if (rows) *rows = b->rows;
-    return LBM_OK;
-}
-
 int lbm_batch_step(lbm_batch *b, int n)
 {
     if (!b || n < 0) return LBM_ERR_INVALID_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
-    if (b->err) return b->err;
+    batch_poll(b, false);
+    if (b->err) return batch_take_err(b);
     if (int rc = batch_ready(b)) return rc;
     if (!b->tuned && n > 0)
         if (int rc = batch_tune(b)) return rc;
-    if (b->persist && b->persist_ok && n >= 2) {
-        BK(d2q9_batch_persist(b->precision == LBM_FP64 ? 0 : 1, b->width, b->d_cases, b->n,
-                              b->d_tiles, b->d_nbr, b->ntiles, b->ctx[0]->cur, n, b->d_flags,
-                              b->d_err, b->stream));
-        batch_advance(b, n);
-        return LBM_OK;
-    }
+    if (b->persist && b->persist_ok && n >= 2) return batch_run_persistent(b, n);
     int left = n;
-    if (left >= BATCH_GRAPH_STEPS) {
-        if (b->ctx[0]->cur == 1) {
-            if (int rc = batch_launch(b, b->d_cases, 1, b->stream)) return rc;
-            batch_advance(b, 1);
+    while (left > 0) {
+        const long long t = b->ctx[0]->step;
+        const long long d = next_diag(b, t);
+        if (d == t) {
+            if (int rc = batch_diag_step(b)) return rc;
             --left;
+            continue;
         }
-        if (left >= BATCH_GRAPH_STEPS) {
-            if (int rc = batch_graph(b)) return rc;
-            const int reps = left / BATCH_GRAPH_STEPS;
-            for (int r = 0; r < reps; ++r) BK(cudaGraphLaunch(b->gexec, b->stream));
-            batch_advance(b, reps * BATCH_GRAPH_STEPS);
-            left -= reps * BATCH_GRAPH_STEPS;
-        }
-    }
-    for (; left > 0; --left) {
-        if (int rc = batch_launch(b, b->d_cases, b->ctx[0]->cur, b->stream)) return rc;
-        batch_advance(b, 1);
+        const int run = (d >= 0 && d - t < left) ? (int)(d - t) : left;
+        if (int rc = batch_run_plain(b, run)) return rc;
+        left -= run;
     }
     return LBM_OK;
+}
+
+int lbm_batch_set_diag_every(lbm_batch *b, int k)
+{
+    if (!b || k < 0) return LBM_ERR_INVALID_ARG;
+    b->diag_every = k;
+    return LBM_OK;
+}
+
+int lbm_batch_last_diagnostics(lbm_batch *b, lbm_diag *out)
+{
+    if (!b || !out) return LBM_ERR_INVALID_ARG;
+    if (!b->has_last_diag) return LBM_ERR_STATE;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (b->diag_pending) {
+        if (cudaEventSynchronize(b->diag_ev) != cudaSuccess) {
+            b->err = LBM_ERR_CUDA;
+            return LBM_ERR_CUDA;
+        }
+    }
+    batch_poll(b, true);
+    for (int c = 0; c < b->n; ++c) fill_diag(status_rec(b->h_status)[c], b->last_diag_step, &out[c]);
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch *b)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        b->err = LBM_ERR_CUDA;
+        return LBM_ERR_CUDA;
+    }
+    batch_poll(b, true);
+    return batch_take_err(b);
 }
 
 int lbm_batch_shape(const lbm_batch *b, int *width, int *rows, int *ntiles)
@@ -1408,10 +1567,24 @@ int lbm_batch_shape(const lbm_batch *b, int *width, int *rows, int *ntiles)
     return LBM_OK;
 }
 
+
+int lbm_batch_tune(lbm_batch *b, int *width, int *rows)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (int rc = batch_ready(b)) return rc;
+    if (int rc = batch_reset_timeout(b)) return rc;
+    if (int rc = batch_tune(b)) return rc;
+    if (width) *width = b->width;
+    if (rows) *rows = b->rows;
+    return LBM_OK;
+}
+
 int lbm_batch_set_shape(lbm_batch *b, int width, int rows)
 {
     if (!b || (width != 64 && width != 128) || rows < 2) return LBM_ERR_INVALID_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
+    if (int rc = batch_reset_timeout(b)) return rc;
     if (int rc = batch_build_tiles(b, width, rows)) return rc;
     b->tuned = 1;
     return LBM_OK;
@@ -1462,7 +1635,6 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaStreamSynchronize(b->stream);
     batch_free(b);
 }
-
 
 }  // extern "C"
 

@@ -3,8 +3,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+
+#include "lbm.h"
 
 namespace wblbm {
 
@@ -21,6 +24,65 @@ struct StepParams {
     T nuv, dnu;          // nu  = nuv  + (phi - phiv) * dnu  (Eq. vis)
     T G[3];              // body force
 };
+
+// ------------------------------------------------ parameters (host only)
+
+// The checks every entry point taking (grid, lattice, params) applies.
+inline int validate_problem(const lbm_grid *g, int lattice, const lbm_params *p)
+{
+    auto finite_pos = [](double v) { return isfinite(v) && v > 0.0; };
+    if (!g || !p) return LBM_ERR_INVALID_ARG;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_ERR_INVALID_ARG;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_ERR_INVALID_ARG;
+    if (lattice == LBM_D2Q9 && g->nz != 1) return LBM_ERR_INVALID_ARG;
+    // population offsets are 32-bit in the kernels (up to 20 arrays: the 19
+    // D3Q19 populations and the FP32 rest population's low word)
+    if ((long long)g->nx * g->ny * g->nz * 20 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->W) || !isfinite(p->sigma) || p->sigma < 0.0) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->M)) return LBM_ERR_INVALID_ARG;
+    if (p->tau_f == 0.0) {
+        if (!finite_pos(p->alpha)) return LBM_ERR_INVALID_ARG;
+    } else if (!isfinite(p->tau_f) || p->tau_f <= 0.5) {
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (!isfinite(p->phi_l) || !isfinite(p->phi_v) || p->phi_l == p->phi_v)
+        return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->rho_l) || !finite_pos(p->rho_v)) return LBM_ERR_INVALID_ARG;
+    if (!finite_pos(p->nu_l) || !finite_pos(p->nu_v)) return LBM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(p->body_force[a])) return LBM_ERR_INVALID_ARG;
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32 &&
+        p->precision != LBM_FP32_F16OFF && p->precision != LBM_FP32_BF16OFF)
+        return LBM_ERR_INVALID_ARG;
+    // 16-bit offset storage is built for the D3Q19 path
+    if ((p->precision == LBM_FP32_F16OFF || p->precision == LBM_FP32_BF16OFF) &&
+        lattice != LBM_D3Q19)
+        return LBM_ERR_INVALID_ARG;
+    if (p->diag_every < 0) return LBM_ERR_INVALID_ARG;
+    return LBM_OK;
+}
+
+// Eqs. beta and suiface_tension solved for kappa and beta; Eq. mobility
+// (tau_f from M and alpha, or alpha from M and a given tau_f).
+struct Derived {
+    double kappa, beta, tau_f, alpha;
+};
+inline Derived derive_params(const lbm_params &p)
+{
+    const double cs2 = 1.0 / 3.0;
+    const double d2 = (p.phi_l - p.phi_v) * (p.phi_l - p.phi_v);
+    Derived d;
+    d.kappa = 3.0 * p.W * p.sigma / (2.0 * d2);
+    d.beta = 12.0 * p.sigma / (p.W * d2 * d2);
+    if (p.tau_f == 0.0) {
+        d.alpha = p.alpha;
+        d.tau_f = 0.5 + p.M / (cs2 * p.alpha);
+    } else {
+        d.tau_f = p.tau_f;
+        d.alpha = p.M / (cs2 * (p.tau_f - 0.5));
+    }
+    return d;
+}
 
 // One CTA's partial diagnostics (8 doubles, FP64 whatever the precision).
 struct DiagPartial {
@@ -54,6 +116,29 @@ struct PassArgs {
     int flip;  // step parity: D2Q9 row tiles reverse their march direction on odd steps
 };
 
+// The kernels' scalars of a problem in the compute type T.
+template <typename T>
+void fill_step_params(StepParams<T> &P, const lbm_grid &g, const lbm_params &p, const Derived &d)
+{
+    const double dphi = p.phi_l - p.phi_v;
+    P.nx = g.nx;
+    P.ny = g.ny;
+    P.nz = g.nz;
+    P.N = (long long)g.nx * g.ny * g.nz;
+    P.kappa = (T)d.kappa;
+    P.beta = (T)d.beta;
+    P.phil = (T)p.phi_l;
+    P.phiv = (T)p.phi_v;
+    P.phibar = (T)(0.5 * (p.phi_l + p.phi_v));
+    P.alpha = (T)d.alpha;
+    P.inv_tauf = (T)(1.0 / d.tau_f);
+    P.rhov = (T)p.rho_v;
+    P.drho = (T)((p.rho_l - p.rho_v) / dphi);
+    P.nuv = (T)p.nu_v;
+    P.dnu = (T)((p.nu_l - p.nu_v) / dphi);
+    for (int a = 0; a < 3; ++a) P.G[a] = (T)p.body_force[a];
+}
+
 // FP32 storage holds the f populations shifted by a uniform equilibrium
 // a = alpha mu_ref: f~_i = f_i - w_i a (i != 0), f~_0 = f_0 + (1 - w_0) a.  A
 // uniform shift of mu in f^eq is an exact symmetry of the discrete step (it
@@ -77,7 +162,8 @@ struct BatchCase {
     StepParams<float> pf;
     void *f[2], *g[2];
     void *S, *S_out;
-    float *eqs;  // the grid's equilibrium shifts {buffer 0, buffer 1, target}
+    float *eqs;    // the grid's equilibrium shifts {buffer 0, buffer 1, target, next target}
+    int recentre;  // FP32: batch diagnostics move the target to the middle of the mu range
 };
 // One CTA's tile of a batch: case, strip x0, rows [y0, yend), march direction.
 struct BatchTile {
@@ -88,20 +174,40 @@ struct BatchTile {
 LaunchShape d2q9_shape(int nx, int ny, int num_sms);
 cudaError_t d2q9_pass(int precision, int pass, const void *params, const PassArgs &a,
                       const LaunchShape &s, cudaStream_t st);
-// one time step of every grid of a batch (strip width 128 or 64)
+// one time step of every grid of a batch (strip width 128 or 64); with
+// partials (one record per tile) the step also writes the FP64 diagnostics
+// partials of its source state
 cudaError_t d2q9_batch_step(int precision, int width, const BatchCase *cases,
-                            const BatchTile *tiles, int ntiles, int parity, cudaStream_t st);
-// nsteps time steps of every grid of a batch in one cooperative launch, one
-// resident CTA per tile (ntiles must not exceed the resident capacity:
-// d2q9_batch_persist_ctas_per_sm x SMs).  nbr: per tile PERSIST_NBMAX + 1
-// ints, the count of the tiles its stencil reaches, then their indices.
-// flags: ntiles + 1 ints, zeroed here (the last is a spare that nothing
-// sets: a neighbour index of ntiles stalls a tile, for fault-injection
-// tests); err: a device int set on a wait timeout.
+                            const BatchTile *tiles, int ntiles, int parity, DiagPartial *partials,
+                            cudaStream_t st);
+// per-grid records from the tiles' partials (tile0[c] .. tile0[c + 1] are
+// grid c's tiles); FP32: also moves each grid's shift target
+cudaError_t d2q9_batch_reduce(int precision, const DiagPartial *partials, const int *tile0,
+                              const BatchCase *cases, int ncases, DiagPartial *records,
+                              cudaStream_t st);
+
+// Several time steps of a batch in one cooperative launch (a queue of
+// (step, tile) pairs; see d2q9_batch_persist_kernel).
 constexpr int PERSIST_NBMAX = 16;
-cudaError_t d2q9_batch_persist(int precision, int width, const BatchCase *cases, int ncases,
-                               const BatchTile *tiles, const int *nbr, int ntiles, int parity,
-                               int nsteps, int *flags, int *err, cudaStream_t st);
+struct PersistArgs {
+    const BatchCase *cases;
+    const BatchTile *tiles;
+    const int *nbr;    // per tile PERSIST_NBMAX + 1 ints: the count of the tiles its
+                       // stencil reaches, then their indices (index ntiles: the spare
+                       // counter nothing sets; fault-injection tests)
+    const int *tile0;  // ncases + 1: first tile of each grid
+    int ntiles, ncases, parity0, nsteps;  // nsteps * ntiles < 2^31
+    int diag_k;        // step of the launch that carries the diagnostics, or -1
+    int *ctr;          // 4 counters, then flags (= ctr + 4): ntiles + 1 step
+                       // counters; all zeroed before the launch
+    int *flags;
+    int *err;          // device word set by a wait that timed out (never cleared here)
+    int *err_host;     // mapped host word set with it (may be null)
+    DiagPartial *partials;  // ntiles
+    DiagPartial *records;   // ncases (device-visible; mapped host memory allowed)
+};
+cudaError_t d2q9_batch_persist(int precision, int width, const PersistArgs &pa, int nctas,
+                               cudaStream_t st);
 int d2q9_batch_persist_ctas_per_sm(int precision, int width);
 cudaError_t d2q9_init(int precision, const void *params, const double *phi0, double *mu_tmp,
                       void *f, void *g, void *S, cudaStream_t st);

@@ -50,41 +50,6 @@ int scratch_address(DiagPartial **out)
     return LBM_OK;
 }
 
-bool pos(double v) { return isfinite(v) && v > 0.0; }
-
-template <typename T>
-void derive(const lbm_grid &g, const lbm_params &p, wblbm::StepParams<T> &P)
-{
-    // same relations as lbm_create: Eqs. beta, suiface_tension, mobility
-    const double dphi = p.phi_l - p.phi_v, d2 = dphi * dphi;
-    const double kappa = 3.0 * p.W * p.sigma / (2.0 * d2);
-    const double beta = 12.0 * p.sigma / (p.W * d2 * d2);
-    double alpha = p.alpha, tau_f;
-    const double cs2 = 1.0 / 3.0;
-    if (p.tau_f == 0.0) {
-        tau_f = 0.5 + p.M / (cs2 * p.alpha);
-    } else {
-        tau_f = p.tau_f;
-        alpha = p.M / (cs2 * (p.tau_f - 0.5));
-    }
-    P.nx = g.nx;
-    P.ny = g.ny;
-    P.nz = g.nz;
-    P.N = (long long)g.nx * g.ny * g.nz;
-    P.kappa = (T)kappa;
-    P.beta = (T)beta;
-    P.phil = (T)p.phi_l;
-    P.phiv = (T)p.phi_v;
-    P.phibar = (T)(0.5 * (p.phi_l + p.phi_v));
-    P.alpha = (T)alpha;
-    P.inv_tauf = (T)(1.0 / tau_f);
-    P.rhov = (T)p.rho_v;
-    P.drho = (T)((p.rho_l - p.rho_v) / dphi);
-    P.nuv = (T)p.nu_v;
-    P.dnu = (T)((p.nu_l - p.nu_v) / dphi);
-    for (int a = 0; a < 3; ++a) P.G[a] = (T)p.body_force[a];
-}
-
 }  // namespace
 
 extern "C" int lbm_diagnostics_noalloc(const lbm_grid *grid, int lattice, const lbm_params *params,
@@ -93,15 +58,9 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_grid *grid, int lattice, const 
 {
     if (!grid || !params || !f || !g || !S_prev || !out) return LBM_ERR_INVALID_ARG;
     const lbm_params &p = *params;
-    if (lattice != LBM_D2Q9 || grid->nx < 1 || grid->ny < 1 || grid->nz != 1)
-        return LBM_ERR_INVALID_ARG;
-    if ((long long)grid->nx * grid->ny * 9 >= (1LL << 32)) return LBM_ERR_INVALID_ARG;
-    if (p.precision != LBM_FP64 && p.precision != LBM_FP32) return LBM_ERR_INVALID_ARG;
-    if (!pos(p.W) || !pos(p.M) || !isfinite(p.sigma) || p.sigma < 0.0 ||
-        !isfinite(p.phi_l) || !isfinite(p.phi_v) || p.phi_l == p.phi_v || !pos(p.rho_l) ||
-        !pos(p.rho_v) || !pos(p.nu_l) || !pos(p.nu_v))
-        return LBM_ERR_INVALID_ARG;
-    if (p.tau_f == 0.0 ? !pos(p.alpha) : (!isfinite(p.tau_f) || p.tau_f <= 0.5))
+    // the checks of lbm_create, then what this entry point supports
+    if (int rc = wblbm::validate_problem(grid, lattice, params)) return rc;
+    if (lattice != LBM_D2Q9 || (p.precision != LBM_FP64 && p.precision != LBM_FP32))
         return LBM_ERR_INVALID_ARG;
 
     int dev = 0, nsm = 0;
@@ -114,10 +73,11 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_grid *grid, int lattice, const 
     DiagPartial *partials = nullptr;
     if (int rc = scratch_address(&partials)) return rc;
 
+    const wblbm::Derived d = wblbm::derive_params(p);
     wblbm::StepParams<double> pd;
     wblbm::StepParams<float> pf;
-    derive(*grid, p, pd);
-    derive(*grid, p, pf);
+    wblbm::fill_step_params(pd, *grid, p, d);
+    wblbm::fill_step_params(pf, *grid, p, d);
     const void *prm = p.precision == LBM_FP64 ? (const void *)&pd : (const void *)&pf;
 
     wblbm::PassArgs a = {};

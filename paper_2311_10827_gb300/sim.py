@@ -205,6 +205,19 @@ class Batch:
         """(on, timed_out) of lbm_batch_persistent."""
         return capi.lbm_batch_persistent(self._h, read_timeout)
 
+    def set_diag_every(self, k):
+        """Fused diagnostics of every grid every k steps (lbm_batch_set_diag_every)."""
+        capi.check(capi.lbm_batch_set_diag_every(self._h, k), "lbm_batch_set_diag_every")
+
+    def last_diagnostics(self):
+        """Records of the last fused diagnostics step, one dict per grid."""
+        rc, recs = capi.lbm_batch_last_diagnostics(self._h, len(self))
+        capi.check(rc, "lbm_batch_last_diagnostics")
+        return [r.as_dict() for r in recs]
+
+    def sync(self):
+        capi.check(capi.lbm_batch_sync(self._h), "lbm_batch_sync")
+
     @property
     def handle(self):
         return self._h

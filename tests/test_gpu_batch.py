@@ -66,7 +66,8 @@ def test_batch_tuning_keeps_state_and_reports_shape(gpu):
     b.step(3)
     before = [b.case(i).get_state() for i in range(len(b))]
     w, r = b.tune()
-    assert w in (64, 128) and r >= 8
+    # the listed row counts (8 .. 128) or the one-wave count of a width (even)
+    assert w in (64, 128) and r >= 2 and r % 2 == 0
     assert b.shape()[:2] == (w, r)
     for i in range(len(b)):
         for x, y in zip(before[i], b.case(i).get_state()):

@@ -1,14 +1,19 @@
 """Multi-step batch launches (lbm_batch_set_persistent): one cooperative
-launch runs many time steps, each tile waiting only for the tiles its stencil
-reaches.  The arithmetic is that of the per-step launches, so the states must
-agree bit for bit after every chunk of steps.  Chunks of uneven length are
-interleaved with diagnostics (which move the FP32 equilibrium shift between
-launches).  The shapes cover:
+launch runs many time steps as a queue of (step, tile) pairs, each tile
+waiting only for itself and the tiles its stencil reaches.  The arithmetic is
+that of the per-step launches, so the states must agree bit for bit after
+every chunk of steps.  Chunks of uneven length are interleaved with
+diagnostics (which move the FP32 equilibrium shift between launches).  The
+shapes cover:
 - ragged strips and row tiles;
 - a grid smaller than one tile, whose only neighbour is itself;
-- both strip widths, and the bench's two 1024^2 grids at 128 x 28.
+- both strip widths, and the bench's two 1024^2 grids at 128 x 28;
+- batches with several times more tiles than resident CTAs (the tiles are
+  walked as a queue every step).
 A wait that timed out would leave NaN in S and set the batch's error word:
-both are checked."""
+both are checked.  The fused batch diagnostics (lbm_batch_set_diag_every)
+are checked against the on-demand diagnostics of the same states, and
+against the exact phi budget of the step (reading R14)."""
 import numpy as np
 import pytest
 
@@ -82,16 +87,107 @@ def test_multistep_equals_per_step_bench_config(gpu):
     assert_same(run_pair(gpu, cases, "fp32", 128, 28, (100, 201)))
 
 
-def test_set_persistent_rejects_shapes_that_do_not_fit(gpu):
-    """Two 4096^2 grids at 64 x 8 tiles: 65536 tiles, far more than resident CTAs."""
-    from paper_2311_10827_gb300 import capi
-    cases = [((4096, 4096), dict(BASE, rho_l=10.0))] * 2
-    b = gpu.Batch(cases, precision="fp32")
+def test_multistep_walks_more_tiles_than_resident_ctas(gpu):
+    """64 grids of the ensemble recipe (seeds 0..63: N from U{64..512}, uneven
+    sizes) at 128 x 28 and 64 x 8 tiles: thousands of tiles, several per
+    resident CTA, walked as a queue every step."""
+    cases = []
+    for seed in range(64):
+        c = wl.ensemble_case(seed)
+        cases.append(((c["n"], c["n"]), dict(BASE, rho_l=c["rho_ratio"]),
+                      wl.droplet(c["n"], c["n"], c["R"], 4.0)))
+    assert_same(run_pair(gpu, cases, "fp32", 128, 28, (3, 30)))
+    small = cases[:16]
+    assert_same(run_pair(gpu, small, "fp64", 64, 8, (5, 2)))
+
+
+def _start_at(b, cases, t0):
+    """Every grid initialised from its phi0 (Eq. H_i initial condition), then
+    set to time t0 (the state unchanged): the diagnostics cadence counts from
+    there, so that no diagnostics step (and no FP32 shift move) comes before
+    the one compared."""
+    for i, (_, _, phi) in enumerate(cases):
+        b.case(i).init_phi(phi)
+        f, g, S = b.case(i).get_state()
+        b.case(i).set_state(f, g, S, step=t0)
+
+
+def _bench_like_cases():
+    return [((300, 140), dict(BASE, rho_l=10.0), wl.droplet(300, 140, 30.0, 4.0)),
+            ((256, 100), dict(BASE, rho_l=100.0), wl.droplet(256, 100, 25.0, 4.0)),
+            ((70, 9), dict(BASE, rho_l=3.0), wl.flat_interface(70, 9, 4.0))]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_diagnostics_match_on_demand(gpu, precision):
+    """Diagnostics every 10 steps from t = 1: the step from t = 10 carries
+    them.  Against lbm_diagnostics of the same state at t = 10 (a separate
+    pass, another tiling of the reduction): FP64 sums to 1e-12 relative,
+    extrema identical.  Per-step and multi-step launches give identical
+    records."""
+    cases = _bench_like_cases()
+    recs = {}
+    for persistent in (False, True):
+        b = gpu.Batch([(sh, prm) for sh, prm, _ in cases], precision=precision)
+        try:
+            _start_at(b, cases, 1)
+            b.set_shape(128, 28)
+            if persistent:
+                b.set_persistent(True)
+            b.set_diag_every(10)
+            b.step(12)
+            r = b.last_diagnostics()
+            assert all(x["step"] == 10 for x in r)
+            recs[persistent] = r
+        finally:
+            b.close()
+    ref = gpu.Batch([(sh, prm) for sh, prm, _ in cases], precision=precision)
     try:
-        b.set_shape(64, 8)
-        with pytest.raises(capi.LbmError):
+        _start_at(ref, cases, 1)
+        ref.set_shape(128, 28)
+        ref.step(9)
+        want = [ref.case(i).diagnostics() for i in range(len(ref))]
+    finally:
+        ref.close()
+    for got, w in zip(recs[False], want):
+        assert w["step"] == 10
+        for k in ("sum_phi", "kinetic_energy", "budget"):
+            assert abs(got[k] - w[k]) <= 1e-12 * abs(w[k]) + 1e-300, (k, got[k], w[k])
+        for k in ("u_max", "mu_min", "mu_max"):
+            assert got[k] == w[k], (k, got[k], w[k])
+        assert not got["nonfinite"]
+    for a, b in zip(recs[False], recs[True]):
+        assert a == b
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_fused_diagnostics_phi_budget(gpu, persistent):
+    """Reading R14: sum phi^{t+1} - sum phi^t = -sum (1.5 S^t - 0.5 S^{t-1}),
+    the budget of the step from t, exactly up to FP64 round-off.  Diagnostics
+    every step, read after each call (FP64, three uneven grids); two-step
+    calls put the records in multi-step launches too."""
+    cases = _bench_like_cases()
+    b = gpu.Batch([(sh, prm) for sh, prm, _ in cases], precision="fp64")
+    try:
+        for i, (_, _, phi) in enumerate(cases):
+            b.case(i).init_phi(phi)
+        b.set_shape(128, 28)
+        if persistent:
             b.set_persistent(True)
-        assert b.persistent()[0] is False
+        b.set_diag_every(1)
+        b.step(6)
+        prev = None
+        for n in (1, 2, 1, 2, 1):
+            b.step(n)
+            r = b.last_diagnostics()
+            if prev is not None and r[0]["step"] == prev[0]["step"] + 1:
+                for x, y in zip(prev, r):
+                    assert abs((y["sum_phi"] - x["sum_phi"]) + x["budget"]) <= \
+                        1e-12 * abs(x["sum_phi"])
+                    assert abs(x["budget"]) > 0.0
+            prev = r
+        # consecutive records: the last step of a call carries the diagnostics
+        assert prev[0]["step"] == 6 + 7 - 1
     finally:
         b.close()
 
@@ -99,8 +195,10 @@ def test_set_persistent_rejects_shapes_that_do_not_fit(gpu):
 def test_stalled_tile_times_out_without_hanging(gpu):
     """Fault injection: tile 0 waits on a counter that nothing sets.  The
     launch must end by itself after the bounded wait (about 2 s of SM clock),
-    report the timeout, and leave non-finite fields that the diagnostics flag;
-    the GPU stays usable (a fresh batch then steps normally)."""
+    report the timeout (the next batch step returns LBM_ERR_TIMEOUT, and
+    keeps returning it until the tiles are rebuilt), and leave non-finite
+    fields that the diagnostics flag; the GPU stays usable (the same batch,
+    rebuilt and re-initialised, and a fresh batch then step normally)."""
     import time
 
     from paper_2311_10827_gb300 import capi
@@ -119,7 +217,17 @@ def test_stalled_tile_times_out_without_hanging(gpu):
         dt = time.perf_counter() - t
         assert timed_out is True
         assert 0.5 < dt < 30.0, dt
+        assert capi.lbm_batch_step(b.handle, 2) == capi.LBM_ERR_TIMEOUT
+        assert capi.lbm_batch_step(b.handle, 2) == capi.LBM_ERR_TIMEOUT
+        assert capi.lbm_batch_sync(b.handle) == capi.LBM_ERR_TIMEOUT
         assert b.case(0).diagnostics()["nonfinite"]
+        b.set_shape(128, 16)  # rebuilt tiles: the injection and the timeout are cleared
+        assert b.persistent(read_timeout=True)[1] is False
+        for i in range(len(b)):
+            b.case(i).init_phi(phi)
+        b.step(4)
+        b.sync()
+        assert not b.case(0).diagnostics()["nonfinite"]
     finally:
         b.close()
     fresh = gpu.Batch(cases, precision="fp32")
