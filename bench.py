@@ -428,14 +428,15 @@ def run_native(args, rank, world, local_rank):
     phi_d = torch.tensor(phi0(n), dtype=torch.float64, device=dev)
     for i in range(len(batch)):
         batch.case(i).init_phi(phi_d)
+    # the tile shape: given, or tuned for the launches that will run
+    multi = not args.per_step
     if args.tile:
         width, rows = (int(v) for v in args.tile.lower().split("x"))
         batch.set_shape(width, rows)
-    else:
-        width, rows = batch.tune()
-    multi = not args.per_step
     if multi:
         batch.set_persistent(True)
+    if not args.tile:
+        width, rows = batch.tune()
     batch.set_diag_every(de)
     # The timed region (exactly K steps between two device synchronisations)
     # is repeated until about --min-time seconds of timed work, so that the
@@ -665,10 +666,14 @@ def run_ensemble(args, rank, world, local_rank):
     b = Batch(cases, precision=args.precision, stream=stream.cuda_stream)
     for i, phi in enumerate(phis):
         b.case(i).init_phi(phi)
-    width, rows = b.tune()
     multi = not args.per_step
+    if args.tile:
+        width, rows = (int(v) for v in args.tile.lower().split("x"))
+        b.set_shape(width, rows)
     if multi:
         b.set_persistent(True)
+    if not args.tile:
+        width, rows = b.tune()
     b.set_diag_every(de)
     ctas = b.shape()[2]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

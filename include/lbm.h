@@ -333,10 +333,16 @@ int lbm_batch_last_diagnostics(lbm_batch *b, lbm_diag *out);
  * (TIMEOUT, NONFINITE) as lbm_batch_step does.  Errors: INVALID_ARG, CUDA. */
 int lbm_batch_sync(lbm_batch *b);
 
-/* Time every candidate tile shape on the current state (the state is left
- * unchanged: candidates write only to scratch) and keep the fastest; report
- * it in *width and *rows (either may be NULL).  Synchronises.  Errors: STATE
- * (a grid not initialised), CUDA. */
+/* Time every candidate tile shape on the current state and keep the
+ * fastest; report it in *width and *rows (either may be NULL).  With
+ * per-step launches the candidates are single steps that write only to
+ * scratch.  With multi-step launches on (lbm_batch_set_persistent) they are
+ * multi-step launches of the grids' own state: the current population
+ * buffers, S, the FP32 equilibrium shifts, the step count and parity are
+ * copied to a temporary device buffer of the state's size first and put
+ * back after, so the state is left unchanged either way.  Synchronises.
+ * Errors: STATE (a grid not initialised), OOM (the temporary buffer), CUDA,
+ * TIMEOUT (a multi-step candidate's wait gave up). */
 int lbm_batch_tune(lbm_batch *b, int *width, int *rows);
 
 /* Current tile shape and number of tiles (CTAs per step). */
@@ -361,10 +367,14 @@ int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
  * the rest population (both buffers) and of S with NaN (so that diagnostics
  * report non-finite fields) and stops; the launch then ends, lbm_batch_step
  * returns LBM_ERR_TIMEOUT from then on, and lbm_batch_persistent reports it.
- * Tunes first if the batch is untuned.  on = 0 returns to per-step launches
- * (CUDA-graph replay).  Single-step calls always launch once per step.
- * Errors: INVALID_ARG (NULL, or on = 1 with a shape whose tiles have more
- * than 16 neighbour tiles), CUDA. */
+ * FP32 batches whose grids all have rows of a multiple of 4 nodes run a
+ * variant that stages each tile's pulls as 16-byte row-segment copies one
+ * iteration ahead (read from L2 only).  Tunes first if the batch is untuned
+ * (timing multi-step launches as lbm_batch_tune does, when every grid is
+ * initialised; else timing single steps).  on = 0 returns to per-step
+ * launches (CUDA-graph replay).  Single-step calls always launch once per
+ * step.  Errors: INVALID_ARG (NULL, or on = 1 with a shape whose tiles have
+ * more than 16 neighbour tiles), OOM, CUDA. */
 int lbm_batch_set_persistent(lbm_batch *b, int on);
 
 /* *on (optional): whether multi-step launches are in use.  *timed_out

@@ -18,6 +18,9 @@
 // stored f value is read once per strip apart from the 4-column halo (served
 // by L2).  A thread's own output row was summed into phi by the same thread
 // one iteration earlier, so its nine pulled f values stay in registers.
+// The pulls are loaded by each thread into registers, or (the FP32
+// multi-step kernel) staged in shared memory one iteration ahead as 16-byte
+// copies of whole row segments.
 // Row tiles march in alternating directions (even tiles down, odd tiles up),
 // so two neighbouring tiles reach their shared boundary rows at the same
 // time and the y-halo rows are served from L2 instead of being re-read from
@@ -105,40 +108,16 @@ __device__ __forceinline__ void pull9(const T *__restrict__ s, unsigned N, unsig
     v[8] = ldp<NC>(s + (8u * N + rp + xm));  // c = (1,-1)
 }
 
-// Per-thread asynchronous copy global -> shared (4 or 8 bytes) and its
-// group fences: a thread's own copies are visible to it after wait_group.
-template <typename T>
-__device__ __forceinline__ void cp_async(T *dst, const T *src)
+// A 16-byte asynchronous copy global -> shared that reads L2 only
+// (cp.async.cg: no L1 allocation), and its group fences: a thread's own
+// copies are visible to it after wait_group, to the CTA after a barrier.
+__device__ __forceinline__ void cp16(float *dst, const float *src)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all_but_one()
-{
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// the nine pull addresses of (x, y) (same order as pull9)
-template <typename T>
-__device__ __forceinline__ void stage9(T *dst, int stride, const T *__restrict__ s, unsigned N,
-                                       unsigned rm, unsigned r0, unsigned rp, unsigned xm,
-                                       unsigned x, unsigned xp)
-{
-    cp_async(dst + 0 * stride, s + (r0 + x));
-    cp_async(dst + 1 * stride, s + (1u * N + rp + x));
-    cp_async(dst + 2 * stride, s + (2u * N + r0 + xm));
-    cp_async(dst + 3 * stride, s + (3u * N + rm + x));
-    cp_async(dst + 4 * stride, s + (4u * N + r0 + xp));
-    cp_async(dst + 5 * stride, s + (5u * N + rm + xm));
-    cp_async(dst + 6 * stride, s + (6u * N + rm + xp));
-    cp_async(dst + 7 * stride, s + (7u * N + rp + xp));
-    cp_async(dst + 8 * stride, s + (8u * N + rp + xm));
-}
 
 // The paired FP32 datapath (add/mul/fma.rn.f32x2): two independent lanes per
 // instruction, each rounding exactly as the scalar instruction would.  The
@@ -194,65 +173,120 @@ struct Occ {
     static constexpr int ctas = threads / nth > 0 ? threads / nth : 1;
 };
 
-// Shared memory of one tile march: the phi and mu rings, the FP32 staging
-// of the f pulls (two stages: the next iteration's phi row is copied in
-// while this iteration runs) and the diagnostics' per-warp partials.  One
-// instance per kernel, whichever tile variants the kernel runs.
+// Shared memory of one tile march outside the staging: the phi and mu rings
+// and the diagnostics' per-warp partials.  One instance per kernel,
+// whichever tile variants the kernel runs.
 template <typename T, int TX>
 struct TileSmem {
     static constexpr int R = 2 * TYB + 3;  // ring depth: writes never hit a row still read
     static constexpr int WP = TX + 4;      // phi ring width (halo 2)
     static constexpr int WM = TX + 2;      // mu ring width (halo 1)
-    static constexpr bool STAGE = sizeof(T) == 4;
-    static constexpr int NS = 2;  // staging depth (FP32)
-    static constexpr int NT = TX * TYB, NFS = sizeof(T) == 4 ? 10 : 9;
+    static constexpr int NT = TX * TYB;
     T phs[R * WP];
     T mus[R * WM];
-    T fst[STAGE ? NS * NFS * NT : 1];
-    T fsh[STAGE ? NS * NFS * 4 * TYB : 1];
     double red[7][NT / 32];
-    // Per-thread diagnostics accumulators, kept here rather than in
-    // registers so that a diagnostics step needs no more registers than a
-    // plain one: the sums of phi, rho |u|^2 / 2, S and S_prev (FP64 for FP64
-    // storage; for FP32 each as an exact FP32 (hi, lo) pair, so that the FP32
-    // step does no FP64 arithmetic per node), the extrema of |u|^2 and mu,
-    // and the tile's non-finite flag.
-    static constexpr int NACC = sizeof(T) == 4 ? 8 : 4;
-    T acc[NACC][NT];
-    T ext[3][NT];
     int bad;
 };
-static_assert(sizeof(TileSmem<float, 128>) <= 48 * 1024, "static shared memory of a CTA");
-static_assert(sizeof(TileSmem<double, 128>) <= 48 * 1024, "static shared memory of a CTA");
+
+// Row-segment staging of the pulls (FP32, rows of a multiple of 4 nodes).
+// Per iteration a stage holds, for each of the TYB thread rows, the ten f
+// segments (populations 0..8 and the rest population's low word) of the phi
+// row two rows ahead, the nine g segments and the S segment of the row being
+// updated.  An f or g segment is the source row of its population (the row
+// shifted by -c_y) over columns x0 - 4 .. x0 + TX + 3, so that a thread's pull
+// from x - c_x is element tx + 4 - c_x; the S segment spans x0 .. x0 + TX - 1.
+// The segments are copied in 16-byte chunks with cp.async.cg, which reads L2
+// only (no L1 allocation), so the same staging is valid in launches whose
+// other CTAs wrote the source rows earlier in the launch.  Two stages: the
+// copies for the next iteration fly while this one computes.
+template <int TX>
+struct SegLayout {
+    static constexpr int W = TX + 8;                      // elements per f / g segment
+    static constexpr int NF = 10, NG = 9;                 // segments per thread row
+    static constexpr int GOFF = TYB * NF * W;             // g segments of a stage
+    static constexpr int SOFF = GOFF + TYB * NG * W;      // S segments of a stage
+    static constexpr int STAGE = SOFF + TYB * TX;         // floats per stage
+    static constexpr int NSEG = TYB * (NF + NG + 1);      // segments per stage
+    static constexpr int LPS = TX / 4;                    // lanes per segment (one main chunk each)
+    static constexpr int SPW = 32 / LPS;                  // segments per warp pass
+    static_assert(TX % 4 == 0 && 32 % LPS == 0 && NSEG % SPW == 0, "segment split");
+    // A diagnostics step lays the same memory out as one f buffer (refilled
+    // once the phi rows are read), two g buffers and then the per-thread
+    // accumulators; S is loaded into registers.
+    static constexpr int DG = TYB * NF * W;               // g buffer 0
+    static constexpr int DACC = DG + 2 * TYB * NG * W;    // accumulators
+    static_assert(DACC + 11 * TX * TYB <= 2 * STAGE, "diagnostics layout");
+};
+
+// Per-thread diagnostics accumulators (a diagnostics pass runs the register
+// path and keeps them where the staging would be): the sums of phi,
+// rho |u|^2 / 2, S and S_prev (FP64 for FP64 storage; for FP32 each as an
+// exact FP32 (hi, lo) pair, so that the FP32 step does no FP64 arithmetic per
+// node), then the extrema of |u|^2 and mu.
+template <typename T>
+struct DiagAcc {
+    static constexpr int NACC = sizeof(T) == 4 ? 8 : 4;
+};
+
+// Dynamic shared memory of a kernel running tiles of width TX: the
+// diagnostics accumulators and, in a kernel that stages (SEGK, FP32), the
+// two stages, whichever is larger.  Only the multi-step kernel stages: the
+// stages take most of the unified L1 / shared memory, which the register
+// path needs as L1 for its loads in flight.
+template <typename T, int TX, bool SEGK = false>
+constexpr int tile_dyn_bytes()
+{
+    constexpr int diag = (DiagAcc<T>::NACC + 3) * TX * TYB * (int)sizeof(T);
+    constexpr int seg = SEGK && sizeof(T) == 4 ? 2 * SegLayout<TX>::STAGE * 4 : 0;
+    return diag > seg ? diag : seg;
+}
+static_assert(sizeof(TileSmem<float, 128>) + tile_dyn_bytes<float, 128, true>() + 1024 <=
+                  228 * 1024 / 4,
+              "four staging FP32 CTAs of width 128 per SM");
+
+// The packed c_y of populations 0..9 (9: the rest population's low word),
+// 2 bits each as c_y + 1.
+constexpr unsigned cy_packed()
+{
+    unsigned v = 0;
+    for (int i = 0; i < 9; ++i) v |= (unsigned)(cyv(i) + 1) << (2 * i);
+    return v | (1u << 18);
+}
+
+// Whether a grid's pulls can be staged in 16-byte chunks: FP32 storage,
+// rows of a multiple of 4 nodes and 16-byte aligned buffers.
+template <typename T>
+__device__ __forceinline__ bool seg_ok(int nx, const void *f, const void *g, const void *S)
+{
+    return sizeof(T) == 4 && (nx & 3) == 0 &&
+           (((unsigned long long)f | (unsigned long long)g | (unsigned long long)S) & 15) == 0;
+}
 
 // One tile: columns [x0, x0 + TX), rows [y0, yend), marching in direction
 // dir (+1 down from y0, -1 up from yend - 1); diagnostics partial record
 // `part` (PASS_DIAG).  Shared by the single-grid and the batched kernels.
-template <typename T, int TX, int PASS, bool NC = true>
-__device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<T> &P,
+// dyn is the kernel's dynamic shared memory (tile_dyn_bytes).  SEG: the pulls
+// are staged as row segments (FP32; seg_ok must hold); else each thread
+// loads its own pulls into registers, through the read-only path (NC: data
+// constant for the launch) or from L2 only (multi-step launches).
+template <typename T, int TX, int PASS, bool NC = true, bool SEG = false>
+__device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const StepParams<T> &P,
                                           const PassArgs &a, int x0, int y0, int yend, int dir,
                                           int part)
 {
     using SM = TileSmem<T, TX>;
+    using SL = SegLayout<TX>;
+    static_assert(!SEG || sizeof(T) == 4, "row-segment staging is FP32");
+    // staged diagnostics step (its own layout of the staging memory)
+    constexpr bool DSEG = SEG && (PASS & PASS_DIAG);
     constexpr int R = SM::R, WP = SM::WP, WM = SM::WM;
     constexpr bool REST_PAIR = sizeof(T) == 4;
-    // Staged pulls (asynchronous copies one iteration ahead) in per-step
-    // launches only.  A multi-step launch reads populations that other CTAs
-    // wrote in the same launch, and those reads must come from L2: the
-    // asynchronous 4-byte copies allocate in L1 (cp.async.ca, the only form
-    // at that size) and returned stale values there although each step's
-    // reads follow the writers' release through an acquire, a fence and a
-    // CTA barrier (measured: batches with more tiles than resident CTAs
-    // drifted from per-step launches by 1e-12 to 1e-2).  So a multi-step
-    // launch pulls with ld.global.cg into registers, one iteration ahead.
-    constexpr bool STAGE = SM::STAGE && NC;
-    constexpr int NT = SM::NT, NFS = SM::NFS;
+    constexpr int NT = SM::NT, NACC = DiagAcc<T>::NACC, NW = NT / 32;
     T *const phs = sm.phs;
     T *const mus = sm.mus;
-    T *const fst = sm.fst;
-    T *const fsh = sm.fsh;
-    T(*const dacc)[NT] = sm.acc;
-    T(*const facc)[NT] = sm.ext;
+    T(*const dacc)[NT] = reinterpret_cast<T(*)[NT]>(dyn + (DSEG ? SL::DACC : 0));
+    T(*const facc)[NT] = dacc + NACC;
+    float *const stg = reinterpret_cast<float *>(dyn);
     int *const dbad = &sm.bad;
     const int lin = threadIdx.y * TX + threadIdx.x;
 
@@ -262,6 +296,8 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
     const int tx = threadIdx.x, ty = threadIdx.y;
     const T *__restrict__ fsrc = static_cast<const T *>(a.f_src);
     const T *__restrict__ gsrc = static_cast<const T *>(a.g_src);
+    constexpr bool NEED_S = (PASS & (PASS_STATE | PASS_DIAG)) != 0;
+    constexpr bool STAGE_S = NEED_S && SEG && !DSEG;  // S staged (else loaded into registers)
 
     // own column (phi ring index tx + 2, mu ring index tx + 1)
     const int xo = x0 + tx;
@@ -292,7 +328,7 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
     // phi = f_0 + rest into ring slot sl, column j
     auto put_phi = [&](int sl, int j, T f0, T rest) { phs[sl * WP + j] = f0 + rest; };
     // phi at row `row` for the own column (keeping the pulled values) and the
-    // halo columns.
+    // halo columns, from the thread's own loads.
     auto phi_row = [&](int row, int sl, T v[9], T &lo) {
         const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
         const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
@@ -308,34 +344,73 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
         }
     };
 
-    // issue the copies of phi row `row`'s pulls into stage st
-    auto issue_phi_row = [&](int row, int st) {
-        const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
-        const unsigned r0 = (unsigned)wrap_row(row, ny, small) * nx;
-        const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
-        T *d = fst + (size_t)st * NFS * NT + lin;
-        stage9(d, NT, fsrc, N, rm, r0, rp, xOm, xO, xOp);
-        if (REST_PAIR) cp_async(d + 9 * NT, fsrc + (9u * N + r0 + xO));
-        if (tx < 4) {
-            T *h = fsh + (size_t)st * NFS * 4 * TYB + ty * 4 + tx;
-            stage9(h, 4 * TYB, fsrc, N, rm, r0, rp, xHm, xH, xHp);
-            if (REST_PAIR) cp_async(h + 9 * 4 * TYB, fsrc + (9u * N + r0 + xH));
-        }
+    // Staged pulls.  Warp w copies segments w*SPW.., (w+NW)*SPW.., ... of the
+    // stage; lane l (within its segment) the main chunk l (columns x0 + 4l..)
+    // and lanes 0 / 1 also the left / right halo chunk.  Chunks never straddle
+    // the periodic seam (nx % 4 == 0).
+    const int lane = lin & 31, wid = lin >> 5;
+    const int l4 = lane % SL::LPS, sub = lane / SL::LPS;
+    const unsigned cMain = SEG ? (unsigned)wrapi(x0 + 4 * l4, nx) : 0u;
+    const unsigned cHalo = SEG ? (unsigned)wrapi(l4 == 0 ? x0 - 4 : x0 + TX, nx) : 0u;
+    const int eHalo = l4 == 0 ? 0 : TX + 4;
+    const bool haloL = l4 < 2;
+    // where the f segments of stage st go and where its g segments go
+    auto fbuf = [&](int st) { return stg + (DSEG ? 0 : st * SL::STAGE); };
+    auto gbuf = [&](int st) {
+        return stg + (DSEG ? SL::DG + st * TYB * SL::NG * SL::W : st * SL::STAGE + SL::GOFF);
     };
-    // phi row from stage st (the copies have landed), keeping the own pulls
-    auto phi_row_staged = [&](int sl, int st, T v[9], T &lo) {
-        const T *d = fst + (size_t)st * NFS * NT + lin;
+    // if doF, the f segments of phi rows mF.. (march coordinates); if doG, the
+    // g (and S) segments of rows mG.. (only rows of the tile); stage st
+    auto issue_stage = [&](int st, bool doF, int mF, bool doG, int mG) {
+        float *const sb = stg + st * SL::STAGE;
+        const float *const fs = reinterpret_cast<const float *>(fsrc);
+        const float *const gs = reinterpret_cast<const float *>(gsrc);
+        const float *const ss = static_cast<const float *>(a.S);
+        for (int grp = wid; grp * SL::SPW < SL::NSEG; grp += NW) {
+            const int s = grp * SL::SPW + sub;
+            const int j = s / (SL::NF + SL::NG + 1), r = s - j * (SL::NF + SL::NG + 1);
+            const float *src;
+            float *dst;
+            int m;
+            bool halo = true;
+            if (r < SL::NF) {
+                if (!doF) continue;
+                m = mF + j;
+                src = fs + (unsigned)r * N;
+                dst = fbuf(st) + (j * SL::NF + r) * SL::W;
+            } else if (r < SL::NF + SL::NG) {
+                m = mG + j;
+                if (!doG || m >= nout) continue;
+                src = gs + (unsigned)(r - SL::NF) * N;
+                dst = gbuf(st) + (j * SL::NG + r - SL::NF) * SL::W;
+            } else {
+                m = mG + j;
+                if (!doG || !STAGE_S || m >= nout) continue;
+                src = ss;
+                dst = sb + SL::SOFF + j * TX - 4;
+                halo = false;
+            }
+            const int pop = r < SL::NF ? r : r - SL::NF;
+            const int cy = r < SL::NF + SL::NG ? (int)((cy_packed() >> (2 * pop)) & 3u) - 1 : 0;
+            const unsigned ro = (unsigned)wrap_row(first + dir * m - cy, ny, small) * nx;
+            cp16(dst + 4 + 4 * l4, src + ro + cMain);
+            if (halo && haloL) cp16(dst + eHalo, src + ro + cHalo);
+        }
+        cp_commit();
+    };
+    // phi row from stage st (thread row ty), keeping the own pulls
+    auto phi_row_seg = [&](int sl, int st, T v[9], T &lo) {
+        const float *F = fbuf(st) + ty * SL::NF * SL::W;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = d[i * NT];
-        lo = REST_PAIR ? d[9 * NT] : T(0);
+        for (int i = 0; i < 9; ++i) v[i] = F[i * SL::W + tx + 4 - cxv(i)];
+        lo = F[9 * SL::W + tx + 4];
         put_phi(sl, tx + 2, v[0], lo + sum_moving(v));
         if (tx < 4) {
-            const T *h = fsh + (size_t)st * NFS * 4 * TYB + ty * 4 + tx;
-            T hv[9];
+            T h[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) hv[i] = h[i * 4 * TYB];
-            const T hlo = REST_PAIR ? h[9 * 4 * TYB] : T(0);
-            put_phi(sl, jH, hv[0], hlo + sum_moving(hv));
+            for (int i = 0; i < 9; ++i) h[i] = F[i * SL::W + jH + 2 - cxv(i)];
+            const T hlo = F[9 * SL::W + jH + 2];
+            put_phi(sl, jH, h[0], hlo + sum_moving(h));
         }
     };
 
@@ -359,11 +434,11 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
         if (tx < 2) mr[jM] = mu_at(sm, s0, sp, jM);
     };
 
-    // diagnostics: sums in FP64; the extrema of |u|^2 and mu and the
-    // non-finite flag are exact in the storage type
+    // diagnostics: sums in FP64 (FP32: exact pairs); the extrema of |u|^2 and
+    // mu and the non-finite flag are exact in the storage type
     if (PASS & PASS_DIAG) {
 #pragma unroll
-        for (int q = 0; q < SM::NACC; ++q) dacc[q][lin] = T(0);
+        for (int q = 0; q < NACC; ++q) dacc[q][lin] = T(0);
         facc[0][lin] = T(0);
         facc[1][lin] = T(INFINITY);
         facc[2][lin] = T(-INFINITY);
@@ -373,17 +448,28 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
     // prologue: phi rows y0-2 .. y0+1 (the own row y0+ty keeps its values),
     // mu rows y0-1 .. y0
     T fcur[9], fnext[9], locur = T(0), lonext = T(0);
-    if (STAGE) {
-        // every copy of the prologue in flight at once
-        issue_phi_row(first + dir * (ty - 2), 1);
-        issue_phi_row(first + dir * ty, 0);
-        cp_commit();
+    if constexpr (DSEG) {
+        // one f buffer: the two phi row pairs one after the other
+        issue_stage(0, true, -2, false, 0);
         cp_wait_all();
-        phi_row_staged(slot(first + dir * (ty - 2)), 1, fnext, lonext);
-        phi_row_staged(slot(first + dir * ty), 0, fcur, locur);
+        __syncthreads();
+        phi_row_seg(slot(first + dir * (ty - 2)), 0, fnext, lonext);
+        __syncthreads();
+        issue_stage(0, true, 0, false, 0);
+        cp_wait_all();
+        __syncthreads();
+        phi_row_seg(slot(first + dir * ty), 0, fcur, locur);
+        __syncthreads();
+        issue_stage(0, true, 2, true, 0);
+    } else if constexpr (SEG) {
+        issue_stage(1, true, -2, false, 0);
+        issue_stage(0, true, 0, false, 0);
+        cp_wait_all();
+        __syncthreads();
+        phi_row_seg(slot(first + dir * (ty - 2)), 1, fnext, lonext);
+        phi_row_seg(slot(first + dir * ty), 0, fcur, locur);
         __syncthreads();  // stage 0 is read before it is refilled
-        issue_phi_row(first + dir * (2 + ty), 0);
-        cp_commit();
+        issue_stage(0, true, 2, true, 0);
     } else {
         phi_row(first + dir * (ty - 2), slot(first + dir * (ty - 2)), fnext, lonext);
         phi_row(first + dir * ty, slot(first + dir * ty), fcur, locur);
@@ -405,28 +491,34 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
         };
         const int row = first + dir * (t + ty);
         const bool out_ok = col_ok && t + ty < nout;
-        // issue the loads of the own node first so they overlap the stencil work
+        const int st = (t / TYB) & 1;
         T gv[9];
         T Sprev = T(0);
         const unsigned nrow = (unsigned)wrap_row(row, ny, small) * nx;
-        {
+        if constexpr (SEG) {
+            // this iteration's stage has landed (own copies) and is visible
+            // (barrier); every read of the other stage (the previous
+            // iteration) is done, so it is refilled for the next iteration
+            // (a diagnostics step refills its one f buffer after the phi rows
+            // are read, below)
+            cp_wait_all();
+            __syncthreads();
+            if (t + TYB < nout) issue_stage(st ^ 1, !DSEG, t + TYB + 2, true, t + TYB);
+            if (DSEG && NEED_S && out_ok)
+                Sprev = __ldcg(static_cast<const T *>(a.S) + (nrow + xo));  // from L2
+            phi_row_seg(ring(2 + ty), st, fnext, lonext);
+        } else {
+            // issue the loads of the own node first so they overlap the stencil work
             const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
             const unsigned rp = (unsigned)wrap_row(row + 1, ny, small) * nx;
             pull9<NC>(gsrc, N, rm, nrow, rp, xOm, xO, xOp, gv);
-            if ((PASS & (PASS_STATE | PASS_DIAG)) && out_ok)
+            if (NEED_S && out_ok)
                 Sprev = NC ? __ldcs(static_cast<const T *>(a.S) + (nrow + xo))
                            : __ldcg(static_cast<const T *>(a.S) + (nrow + xo));  // from L2
-        }
-        if (STAGE) {
-            const int st = (t / TYB) & 1;
-            if (t + TYB < nout) issue_phi_row(first + dir * (t + TYB + 2 + ty), st ^ 1);
-            cp_commit();  // possibly empty: one group per iteration
-            cp_wait_all_but_one();
-            phi_row_staged(ring(2 + ty), st, fnext, lonext);
-        } else {
             phi_row(first + dir * (t + 2 + ty), ring(2 + ty), fnext, lonext);
         }
         __syncthreads();
+        if (DSEG && t + TYB < nout) issue_stage(0, true, t + TYB + 2, false, 0);
         mu_row(ring(1 + ty - dir), ring(1 + ty), ring(1 + ty + dir));
         __syncthreads();
 
@@ -434,6 +526,12 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
         rb += TYB;
         rb = rb >= R ? rb - R : rb;
         if (out_ok) {
+            if constexpr (SEG) {
+                const float *G = gbuf(st) + ty * SL::NG * SL::W;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) gv[i] = G[i * SL::W + tx + 4 - cxv(i)];
+                if (STAGE_S) Sprev = stg[st * SL::STAGE + SL::SOFF + ty * TX + tx];
+            }
             const T *pm = phs + sm * WP;
             const T *p0 = phs + s0 * WP;
             const T *pp = phs + sp * WP;
@@ -676,7 +774,7 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
         for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
         locur = lonext;
     }
-    if (!NC) cp_wait_all();  // the next step of a multi-step launch reuses the stages
+    if (SEG) cp_wait_all();  // nothing in flight when the tile ends
 
     if (PASS & PASS_DIAG) {
         __syncthreads();  // every flag write of the march is done
@@ -694,9 +792,7 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
         T d_u2 = facc[0][lin], d_mumin = facc[1][lin], d_mumax = facc[2][lin],
           d_bad = *dbad ? T(1) : T(0);
         warp_reduce(d_phi, d_E, d_u2, d_mumin, d_mumax, d_bud, d_bad);
-        constexpr int NW = TX * TYB / 32;
         double(*red)[NW] = sm.red;
-        const int lane = (ty * TX + tx) & 31, wid = (ty * TX + tx) >> 5;
         if (lane == 0) {
             red[0][wid] = d_phi;
             red[1][wid] = d_E;
@@ -731,6 +827,9 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, const StepParams<
     }
 }
 
+// The kernels' dynamic shared memory (tile_dyn_bytes of their tile width).
+extern __shared__ float4 tile_dyn[];
+
 // Single grid: CTA (bx, by) owns strip bx and row tile by; even row tiles
 // march down, odd ones up, so neighbouring tiles meet at their shared rows.
 template <typename T, int TX, int PASS>
@@ -742,8 +841,8 @@ __global__ void __launch_bounds__((Occ<T, PASS, TX>::nth), (Occ<T, PASS, TX>::ct
     // reversed on every other step
     const int dir = ((blockIdx.y & 1) ? -1 : 1) * (a.flip ? -1 : 1);
     __shared__ TileSmem<T, TX> sm;
-    d2q9_tile<T, TX, PASS>(sm, P, a, blockIdx.x * TX, y0, min(y0 + rows, P.ny), dir,
-                           blockIdx.y * gridDim.x + blockIdx.x);
+    d2q9_tile<T, TX, PASS>(sm, reinterpret_cast<T *>(tile_dyn), P, a, blockIdx.x * TX, y0,
+                           min(y0 + rows, P.ny), dir, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Batched: CTA k runs tile k of a flat tile table over many independent grids
@@ -771,7 +870,8 @@ __global__ void __launch_bounds__((Occ<T, PASS, TX>::nth), (Occ<T, PASS, TX>::ct
     a.eqs_dst = c.eqs + (parity ^ 1);
     a.eqs_target = c.eqs + 2;
     __shared__ TileSmem<T, TX> sm;
-    d2q9_tile<T, TX, PASS>(sm, P, a, t.x0, t.y0, t.yend, parity ? -t.dir : t.dir, blockIdx.x);
+    d2q9_tile<T, TX, PASS>(sm, reinterpret_cast<T *>(tile_dyn), P, a, t.x0, t.y0, t.yend,
+                           parity ? -t.dir : t.dir, blockIdx.x);
 }
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p)
@@ -796,17 +896,25 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v)
 // launch, and the oldest unfinished step of any tile can always proceed).
 constexpr long long PERSIST_WAIT_CYCLES = 4000000000LL;
 
-// Per-grid reduction of the tiles' FP64 diagnostics partials (a fixed order,
-// so the same partials always give the same record), one thread per grid.
-// shift_slot >= 0 (FP32 storage): the grid's next equilibrium-shift target,
-// alpha times the middle of the mu range (kept if the record is not finite or
-// re-centring is off), is written to eqs[shift_slot].
-__device__ void reduce_cases(const DiagPartial *part, const int *tile0, const BatchCase *cases,
-                             int ncases, DiagPartial *records, int shift_slot, int tid, int nthr)
+// Threads that reduce one grid's diagnostics partials.
+constexpr int RG = 128;
+
+// Reduction of grid c's tile partials (tiles k0 .. k1-1) into its record, in
+// a fixed order whatever the caller: thread i < RG sums tiles k0 + i,
+// k0 + i + RG, ... in turn, a fixed xor butterfly combines each warp, and
+// thread 0 combines the four warps as (w0 + w1) + (w2 + w3).  Every thread
+// of the CTA calls it (two barriers); red holds 7 x 4 doubles of shared
+// memory.  shift_slot >= 0 (FP32 storage): the grid's next
+// equilibrium-shift target, alpha times the middle of the mu range (kept if
+// the record is not finite or re-centring is off), is written to
+// eqs[shift_slot].
+__device__ void reduce_case(const DiagPartial *part, int k0, int k1, const BatchCase &cs,
+                            DiagPartial *record, int shift_slot, int tid, double *red)
 {
-    for (int c = tid; c < ncases; c += nthr) {
+    if (tid < RG) {
         double s0 = 0.0, s1 = 0.0, mx = 0.0, mn = DBL_MAX, mxm = -DBL_MAX, s2 = 0.0, bad = 0.0;
-        for (int k = tile0[c]; k < tile0[c + 1]; ++k) {
+#pragma unroll 4
+        for (int k = k0 + tid; k < k1; k += RG) {
             const DiagPartial *p = part + k;  // written by other CTAs: read from L2
             s0 += __ldcg(&p->sum_phi);
             s1 += __ldcg(&p->E);
@@ -816,33 +924,63 @@ __device__ void reduce_cases(const DiagPartial *part, const int *tile0, const Ba
             s2 += __ldcg(&p->budget);
             bad = fmax(bad, __ldcg(&p->nonfinite));
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mxm = fmax(mxm, __shfl_xor_sync(0xffffffffu, mxm, o));
+            bad = fmax(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+        }
+        if ((tid & 31) == 0) {
+            const int w = tid >> 5;
+            red[0 * 4 + w] = s0;
+            red[1 * 4 + w] = s1;
+            red[2 * 4 + w] = mx;
+            red[3 * 4 + w] = mn;
+            red[4 * 4 + w] = mxm;
+            red[5 * 4 + w] = s2;
+            red[6 * 4 + w] = bad;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        auto sum4 = [&](int f) { return (red[f * 4] + red[f * 4 + 1]) + (red[f * 4 + 2] + red[f * 4 + 3]); };
+        auto max4 = [&](int f) { return fmax(fmax(red[f * 4], red[f * 4 + 1]), fmax(red[f * 4 + 2], red[f * 4 + 3])); };
+        auto min4 = [&](int f) { return fmin(fmin(red[f * 4], red[f * 4 + 1]), fmin(red[f * 4 + 2], red[f * 4 + 3])); };
         DiagPartial r;
-        r.sum_phi = s0;
-        r.E = s1;
-        r.u2max = mx;
-        r.mu_min = mn;
-        r.mu_max = mxm;
-        r.budget = s2;
-        r.nonfinite = bad;
+        r.sum_phi = sum4(0);
+        r.E = sum4(1);
+        r.u2max = max4(2);
+        r.mu_min = min4(3);
+        r.mu_max = max4(4);
+        r.budget = sum4(5);
+        r.nonfinite = max4(6);
         r.pad = 0.0;
-        records[c] = r;
+        *record = r;
         if (shift_slot >= 0) {
-            float *e = cases[c].eqs;
+            float *e = cs.eqs;
             float tgt = e[2];
-            const double a = cases[c].pd.alpha * 0.5 * (mn + mxm);
-            if (cases[c].recentre && bad == 0.0 && isfinite(a)) tgt = (float)a;
+            const double al = cs.pd.alpha * 0.5 * (r.mu_min + r.mu_max);
+            if (cs.recentre && r.nonfinite == 0.0 && isfinite(al)) tgt = (float)al;
             e[shift_slot] = tgt;
         }
     }
+    __syncthreads();
 }
 
 // Per-step launches: records of the step that carried the diagnostics; the
 // FP32 target moves at once (the next launch writes with it).
-__global__ void d2q9_batch_reduce_kernel(const DiagPartial *__restrict__ part,
-                                         const int *__restrict__ tile0, const BatchCase *cases,
-                                         int ncases, DiagPartial *records, int shift_slot)
+// One CTA of RG threads per grid.
+__global__ void __launch_bounds__(RG) d2q9_batch_reduce_kernel(const DiagPartial *__restrict__ part,
+                                                               const int *__restrict__ tile0,
+                                                               const BatchCase *cases,
+                                                               DiagPartial *records, int shift_slot)
 {
-    reduce_cases(part, tile0, cases, ncases, records, shift_slot, threadIdx.x, blockDim.x);
+    __shared__ double red[7 * 4];
+    const int c = blockIdx.x;
+    reduce_case(part, tile0[c], tile0[c + 1], cases[c], records + c, shift_slot, threadIdx.x, red);
 }
 
 // Several time steps of a batch in one cooperative launch.  The work is a
@@ -858,17 +996,19 @@ __global__ void d2q9_batch_reduce_kernel(const DiagPartial *__restrict__ part,
 // still running.  Progress: the pair with the lowest ticket still unfinished
 // only waits on pairs with lower tickets, all finished.
 //
+// SEGK (FP32): the variant that stages each tile's pulls as row segments
+// (grids whose rows are a multiple of 4 nodes; others run the register
+// path), diagnostics steps included, with the shared-memory carveout that
+// the staging CTAs need.
+//
 // Memory ordering of the pulls.  Every population, S and phi value that
-// other tiles write during the launch is read with ld.global.cg (L2 only):
-// the tile routine runs without its L1-allocating asynchronous staging here
-// (NC false).  The writer CTA stores, passes bar.sync, and its thread 0
+// other tiles write during the launch is read from L2 only: by the 16-byte
+// row-segment copies (cp.async.cg) or, on the register path, by
+// ld.global.cg.  The writer CTA stores, passes bar.sync, and its thread 0
 // fences and does st.release.gpu on the tile's counter; a polling lane of
 // the reader does ld.acquire.gpu, observes the count, fences, and the CTA
-// passes bar.sync before any read of the next step.  With the asynchronous
-// 4-byte copies (cp.async.ca, which allocate in L1) some reads returned
-// values older than that chain allows (batches with more tiles than
-// resident CTAs drifted from per-step launches), so no read of this
-// launch's data goes through L1.
+// passes bar.sync before any copy or load of the next step is issued.  No
+// read of this launch's data goes through L1.
 //
 // FP32 equilibrium shift: the source buffer's shift is the stored one at
 // step 0 and the target after it (what step 0 wrote with); the target is
@@ -883,7 +1023,7 @@ __global__ void d2q9_batch_reduce_kernel(const DiagPartial *__restrict__ part,
 // fills the tile's rest population (both buffers) and S with NaN (so the
 // diagnostics report non-finite fields) and ends the CTA; CTAs waiting on it
 // or taking a new pair see *err and end too.
-template <typename T, int TX>
+template <typename T, int TX, bool SEGK>
 __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_STATE, TX>::ctas))
     d2q9_batch_persist_kernel(const PersistArgs pa)
 {
@@ -895,8 +1035,15 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
     // the ticket counter, each taken one tile ahead so that its atomic's
     // latency hides behind the tile's work.
     const bool fixed = pa.ntiles <= (int)gridDim.x;
+    // the next launch's counters (this launch uses the other set)
+    for (int i = blockIdx.x * NTH + lin; i < pa.nctr; i += gridDim.x * NTH) pa.ctr_next[i] = 0;
     if (fixed && (int)blockIdx.x >= pa.ntiles) return;
-    __shared__ int s_next, s_abort, s_diag, s_stop;
+    // s_next is double-buffered by the CTA's pair count: thread 0 writes the
+    // slot of pair it at the top of pair it, before any barrier, while the
+    // other warps may still be reading the slot of pair it - 1; the slot of
+    // pair it - 2 was read by every thread before the barriers of pair it - 1
+    __shared__ int s_next[2], s_abort, s_diag, s_stop;
+    int it = 0;
     __shared__ TileSmem<T, TX> sm;
     int tk = blockIdx.x;
     while (tk < total) {
@@ -905,7 +1052,7 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
         // after the tile, so that neither round trip delays it
         int err_seen = 0;
         if (lin == 0) {
-            if (!fixed) s_next = atomicAdd(pa.ctr, 1) + (int)gridDim.x;
+            if (!fixed) s_next[it & 1] = atomicAdd(pa.ctr, 1) + (int)gridDim.x;
             err_seen = ld_relaxed_gpu(pa.err);
         }
         const BatchTile t = pa.tiles[ti];
@@ -972,41 +1119,55 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
         a.eqs_target = c.eqs + 2;
         a.flip = 0;
         const int dir = parity ? -t.dir : t.dir;
-        if (k == pa.diag_k)
-            d2q9_tile<T, TX, PASS_STATE | PASS_DIAG, false>(sm, P, a, t.x0, t.y0, t.yend, dir, ti);
-        else
-            d2q9_tile<T, TX, PASS_STATE, false>(sm, P, a, t.x0, t.y0, t.yend, dir, ti);
+        T *const dyn = reinterpret_cast<T *>(tile_dyn);
+        const bool seg = SEGK && seg_ok<T>(P.nx, a.f_src, a.g_src, a.S);
+        if (k == pa.diag_k) {
+            if (seg)
+                d2q9_tile<T, TX, PASS_STATE | PASS_DIAG, false, SEGK>(sm, dyn, P, a, t.x0, t.y0,
+                                                                       t.yend, dir, ti);
+            else
+                d2q9_tile<T, TX, PASS_STATE | PASS_DIAG, false>(sm, dyn, P, a, t.x0, t.y0, t.yend,
+                                                                 dir, ti);
+        } else if (seg) {
+            d2q9_tile<T, TX, PASS_STATE, false, SEGK>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti);
+        } else {
+            d2q9_tile<T, TX, PASS_STATE, false>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti);
+        }
         __syncthreads();  // every output of the step (and its partial) is stored
         // counters of the launch's last steps (one atomic per tile each):
-        // the last tile of the diagnostics step reduces the partials; the
-        // last tile of the final step (then every pair is done) records the
-        // final shift, after the reduction (ctr[3] = 1 once it is written)
+        // the last tile of a grid in the diagnostics step reduces that grid's
+        // partials (ctr[3] counts the grids reduced); the last tile of the
+        // final step (then every pair is done) records the final shift, after
+        // every reduction
         if (lin == 0) {
             __threadfence();
             st_release_gpu(pa.flags + ti, k + 1);
             int fl = 0;
-            if (k == pa.diag_k && atomicAdd(pa.ctr + 1, 1) == pa.ntiles - 1) fl |= 1;
+            if (k == pa.diag_k &&
+                atomicAdd(pa.case_ctr + t.c, 1) == pa.tile0[t.c + 1] - pa.tile0[t.c] - 1)
+                fl |= 1;
             if (k == pa.nsteps - 1 && atomicAdd(pa.ctr + 2, 1) == pa.ntiles - 1) fl |= 2;
             s_diag = fl;
             s_stop = err_seen;
         }
         __syncthreads();
-        const int next = fixed ? tk + pa.ntiles : s_next;  // read before the next barrier
+        const int next = fixed ? tk + pa.ntiles : s_next[it & 1];
+        ++it;
         const int fl = s_diag, stop = s_stop;
-        if (fl & 1) {  // every partial of the diagnostics step is written
+        if (fl & 1) {  // every partial of this grid's diagnostics step is written
             __threadfence();
-            reduce_cases(pa.partials, pa.tile0, pa.cases, pa.ncases, pa.records,
-                         sizeof(T) == 4 ? 3 : -1, lin, NTH);
-            __syncthreads();
+            reduce_case(pa.partials, pa.tile0[t.c], pa.tile0[t.c + 1], pa.cases[t.c],
+                        pa.records + t.c, sizeof(T) == 4 ? 3 : -1, lin, &sm.red[0][0]);
             if (lin == 0) {
                 __threadfence();
-                st_release_gpu(pa.ctr + 3, 1);
+                atomicAdd(pa.ctr + 3, 1);
             }
         }
-        if (fl & 2) {  // every pair is done; wait for the reduction if there is one
+        if (fl & 2) {  // every pair is done; wait for the reductions if there are any
             if (lin == 0 && pa.diag_k >= 0) {
                 const long long t0 = clock64();
-                while (ld_acquire_gpu(pa.ctr + 3) == 0 && clock64() - t0 < PERSIST_WAIT_CYCLES)
+                while (ld_acquire_gpu(pa.ctr + 3) < pa.ncases &&
+                       clock64() - t0 < PERSIST_WAIT_CYCLES)
                     __nanosleep(64);
             }
             __syncthreads();
@@ -1112,13 +1273,36 @@ __global__ void d2q9_set_state_k(int nx, int ny, T *__restrict__ f, T *__restric
 
 constexpr int TXW = 128;  // strip width (columns per CTA)
 
+// The staging multi-step kernel's dynamic shared memory limit (above the
+// default 48 KB) and shared-memory carveout (all of the unified L1 / shared
+// memory: four staging CTAs per SM, whose copies bypass L1), set once per
+// device.
+template <int TX>
+cudaError_t seg_attrs()
+{
+    static int done[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    const void *k = (const void *)d2q9_batch_persist_kernel<float, TX, true>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tile_dyn_bytes<float, TX, true>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+    return e;
+}
+
 template <typename T, int PASS>
 cudaError_t launch_pass(const void *params, const PassArgs &a, const LaunchShape &s,
                         cudaStream_t st)
 {
     const StepParams<T> &P = *static_cast<const StepParams<T> *>(params);
+    constexpr int dyn = tile_dyn_bytes<T, TXW>();
     dim3 grid(s.grid_x, s.grid_y), block(TXW, TYB);
-    d2q9_pass_kernel<T, TXW, PASS><<<grid, block, 0, st>>>(P, a, s.rows);
+    d2q9_pass_kernel<T, TXW, PASS><<<grid, block, dyn, st>>>(P, a, s.rows);
     return cudaGetLastError();
 }
 
@@ -1144,11 +1328,12 @@ cudaError_t launch_batch_t(const BatchCase *cases, const BatchTile *tiles, int n
                            DiagPartial *partials, cudaStream_t st)
 {
     dim3 block(TX, TYB);
+    constexpr int dyn = tile_dyn_bytes<T, TX>();
     if (partials)
         d2q9_batch_kernel<T, TX, PASS_STATE | PASS_DIAG>
-            <<<ntiles, block, 0, st>>>(cases, tiles, parity, partials);
+            <<<ntiles, block, dyn, st>>>(cases, tiles, parity, partials);
     else
-        d2q9_batch_kernel<T, TX, PASS_STATE><<<ntiles, block, 0, st>>>(cases, tiles, parity, nullptr);
+        d2q9_batch_kernel<T, TX, PASS_STATE><<<ntiles, block, dyn, st>>>(cases, tiles, parity, nullptr);
     return cudaGetLastError();
 }
 
@@ -1169,54 +1354,73 @@ cudaError_t d2q9_batch_reduce(int precision, const DiagPartial *partials, const 
                               const BatchCase *cases, int ncases, DiagPartial *records,
                               cudaStream_t st)
 {
-    d2q9_batch_reduce_kernel<<<1, 256, 0, st>>>(partials, tile0, cases, ncases, records,
-                                                 precision == 0 ? -1 : 2);
+    d2q9_batch_reduce_kernel<<<ncases, RG, 0, st>>>(partials, tile0, cases, records,
+                                                     precision == 0 ? -1 : 2);
     return cudaGetLastError();
 }
 
 namespace {
 
-template <typename T, int TX>
+template <typename T, int TX, bool SEGK>
 cudaError_t launch_persist_t(const PersistArgs &pa, int nctas, cudaStream_t st)
 {
-    // counters (ticket, diagnostics tiles done, final-step tiles done, the
-    // reduction's flag), then the tiles' step counters and the spare one
-    // that nothing sets (fault-injection tests)
-    cudaError_t e = cudaMemsetAsync(pa.ctr, 0, (4 + (size_t)pa.ntiles + 1) * sizeof(int), st);
+    constexpr int dyn = tile_dyn_bytes<T, TX, SEGK>();
+    cudaError_t e = SEGK ? seg_attrs<TX>() : cudaSuccess;
     if (e != cudaSuccess) return e;
+    // The counters (ticket, unused, final-step tiles done, grids reduced; the
+    // tiles' step counters; the spare one that nothing sets, for
+    // fault-injection tests; the grids' diagnostics tiles done) are zero:
+    // the previous launch on the other set zeroed this one.
     void *args[] = {(void *)&pa};
-    e = cudaLaunchCooperativeKernel((const void *)d2q9_batch_persist_kernel<T, TX>, dim3(nctas),
-                                    dim3(TX, TYB), args, 0, st);
-    return e;
+    return cudaLaunchCooperativeKernel((const void *)d2q9_batch_persist_kernel<T, TX, SEGK>,
+                                       dim3(nctas), dim3(TX, TYB), args, dyn, st);
 }
 
-template <typename T, int TX>
+template <typename T, int TX, bool SEGK>
 int persist_ctas_per_sm_t()
 {
     int n = 0;
+    constexpr int dyn = tile_dyn_bytes<T, TX, SEGK>();
+    if (SEGK && seg_attrs<TX>() != cudaSuccess) return 0;
     const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, d2q9_batch_persist_kernel<T, TX>, TX * TYB, 0);
+        &n, d2q9_batch_persist_kernel<T, TX, SEGK>, TX * TYB, dyn);
     return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace
 
-cudaError_t d2q9_batch_persist(int precision, int width, const PersistArgs &pa, int nctas,
-                               cudaStream_t st)
+cudaError_t d2q9_prepare()
 {
-    if (pa.flags != pa.ctr + 4) return cudaErrorInvalidValue;
-    if (precision == 0)
-        return width == 64 ? launch_persist_t<double, 64>(pa, nctas, st)
-                           : launch_persist_t<double, 128>(pa, nctas, st);
-    return width == 64 ? launch_persist_t<float, 64>(pa, nctas, st)
-                       : launch_persist_t<float, 128>(pa, nctas, st);
+    const cudaError_t e = seg_attrs<128>();
+    return e != cudaSuccess ? e : seg_attrs<64>();
 }
 
-int d2q9_batch_persist_ctas_per_sm(int precision, int width)
+cudaError_t d2q9_batch_persist(int precision, int width, bool seg, const PersistArgs &pa,
+                               int nctas, cudaStream_t st)
+{
+    if (pa.flags != pa.ctr + 4 || pa.case_ctr != pa.flags + pa.ntiles + 1 ||
+        pa.nctr != pa.ntiles + 5 + pa.ncases)
+        return cudaErrorInvalidValue;
+    if (precision == 0)
+        return width == 64 ? launch_persist_t<double, 64, false>(pa, nctas, st)
+                           : launch_persist_t<double, 128, false>(pa, nctas, st);
+    if (seg)
+        return width == 64 ? launch_persist_t<float, 64, true>(pa, nctas, st)
+                           : launch_persist_t<float, 128, true>(pa, nctas, st);
+    return width == 64 ? launch_persist_t<float, 64, false>(pa, nctas, st)
+                       : launch_persist_t<float, 128, false>(pa, nctas, st);
+}
+
+int d2q9_batch_persist_ctas_per_sm(int precision, int width, bool seg)
 {
     if (precision == 0)
-        return width == 64 ? persist_ctas_per_sm_t<double, 64>() : persist_ctas_per_sm_t<double, 128>();
-    return width == 64 ? persist_ctas_per_sm_t<float, 64>() : persist_ctas_per_sm_t<float, 128>();
+        return width == 64 ? persist_ctas_per_sm_t<double, 64, false>()
+                           : persist_ctas_per_sm_t<double, 128, false>();
+    if (seg)
+        return width == 64 ? persist_ctas_per_sm_t<float, 64, true>()
+                           : persist_ctas_per_sm_t<float, 128, true>();
+    return width == 64 ? persist_ctas_per_sm_t<float, 64, false>()
+                       : persist_ctas_per_sm_t<float, 128, false>();
 }
 
 LaunchShape d2q9_shape(int nx, int ny, int num_sms)

@@ -473,6 +473,7 @@ int create_impl(const lbm_grid *grid, int lattice, const lbm_params *params, voi
     }
     memset(ctx->hres, 0, 2 * sizeof(DiagPartial));
     if ((ctx->codec >= 0 && reset_scales(ctx) != LBM_OK) || set_eq_shift(ctx, 0.0f) != LBM_OK ||
+        (lattice == LBM_D2Q9 && d2q9_prepare() != cudaSuccess) ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         free_all(ctx);
@@ -950,8 +951,13 @@ struct lbm_batch {
     // multi-step launches (a queue of (step, tile) pairs per cooperative launch)
     int persist;     // requested
     int persist_ok;  // the current tiles have neighbour lists
+    int seg;         // FP32 and every grid's rows a multiple of 4 nodes: the
+                     // multi-step launches stage their pulls as row segments
     int *d_nbr;      // per tile: count, then up to PERSIST_NBMAX neighbour tiles
-    int *d_ctr;      // 4 counters, then per tile the steps completed; one spare (never set)
+    int *d_ctr;      // two sets, used by alternate launches, each: 4 counters, per tile
+                     // the steps completed, one spare (never set), then per grid
+                     // the tiles done with the diagnostics step (batch_nctr ints)
+    int ctr_sel;     // the set the next multi-step launch uses (the other is zero)
     int *d_err;      // set by a wait that timed out
     int persist_cap; // tiles d_nbr and d_ctr hold
     // fused diagnostics
@@ -1073,14 +1079,17 @@ int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int 
         b->d_ctr = nullptr;
         b->persist_cap = 0;
         if (grow((void **)&b->d_nbr, &cap_nbr, count * stride, sizeof(int)) ||
-            grow((void **)&b->d_ctr, &cap_ctr, count + 5, sizeof(int))) {
+            grow((void **)&b->d_ctr, &cap_ctr, 2 * (count + 5 + b->n), sizeof(int))) {
             free(nb);
             return LBM_ERR_OOM;
         }
         b->persist_cap = count;
     }
-    const cudaError_t e =
-        cudaMemcpy(b->d_nbr, nb, (size_t)count * stride * sizeof(int), cudaMemcpyHostToDevice);
+    // both counter sets start at zero; each launch zeroes the other one
+    cudaError_t e = cudaMemset(b->d_ctr, 0, 2 * ((size_t)count + 5 + b->n) * sizeof(int));
+    b->ctr_sel = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_nbr, nb, (size_t)count * stride * sizeof(int), cudaMemcpyHostToDevice);
     free(nb);
     if (e != cudaSuccess) {
         b->err = LBM_ERR_CUDA;
@@ -1197,7 +1206,7 @@ int batch_tune(lbm_batch *b)
         int cand[NR + 1], nc = 0;
         for (int ri = 0; ri < NR; ++ri) cand[nc++] = rowsc[ri];
         const int per_sm = d2q9_batch_persist_ctas_per_sm(b->precision == LBM_FP64 ? 0 : 1,
-                                                          widths[wi]);
+                                                          widths[wi], b->seg != 0);
         const long long slots = (long long)(per_sm > 0 ? per_sm : 4) * b->nsm;
         for (int r = 2; r <= 256; r += 2)
             if (count_tiles(b, widths[wi], r) <= slots) {
@@ -1323,13 +1332,17 @@ int batch_run_persistent(lbm_batch *b, int n)
         pa.parity0 = b->ctx[0]->cur;
         pa.nsteps = m;
         pa.diag_k = diag_k;
-        pa.ctr = b->d_ctr;
-        pa.flags = b->d_ctr + 4;
+        const size_t nctr = (size_t)b->ntiles + 5 + b->n;  // ints per counter set
+        pa.ctr = b->d_ctr + (size_t)b->ctr_sel * nctr;
+        pa.ctr_next = b->d_ctr + (size_t)(b->ctr_sel ^ 1) * nctr;
+        pa.nctr = (int)nctr;
+        pa.flags = pa.ctr + 4;
+        pa.case_ctr = pa.flags + b->ntiles + 1;
         pa.err = b->d_err;
         pa.err_host = &b->d_status->err;
         pa.partials = b->d_partials;
         pa.records = status_rec(b->d_status);
-        const int per_sm = d2q9_batch_persist_ctas_per_sm(prec, b->width);
+        const int per_sm = d2q9_batch_persist_ctas_per_sm(prec, b->width, b->seg != 0);
         if (per_sm < 1) {
             b->err = LBM_ERR_CUDA;
             return LBM_ERR_CUDA;
@@ -1337,7 +1350,8 @@ int batch_run_persistent(lbm_batch *b, int n)
         // one CTA per tile when they all fit at once, else a queue over every slot
         const long long pairs = (long long)m * b->ntiles, slots = (long long)per_sm * b->nsm;
         const int nctas = b->ntiles <= slots ? b->ntiles : (int)(pairs < slots ? pairs : slots);
-        BK(d2q9_batch_persist(prec, b->width, pa, nctas, b->stream));
+        BK(d2q9_batch_persist(prec, b->width, b->seg != 0, pa, nctas, b->stream));
+        b->ctr_sel ^= 1;
         if (diag_k >= 0) {
             BK(cudaEventRecord(b->diag_ev, b->stream));
             b->diag_pending = 1;
@@ -1391,6 +1405,116 @@ int batch_run_plain(lbm_batch *b, int n)
 }
 
 // a rebuild of the tiles clears a timeout: the error words and the sticky error
+// Tile shape for multi-step launches: each candidate (the per-step
+// tuner's list, plus for each width the shortest tiles that fit one wave
+// and two waves of resident CTAs) is timed as multi-step launches on the
+// grids' own state, with diagnostics off.  The state the steps change (the
+// current population buffers, S, the FP32 equilibrium shifts, the step
+// count and parity) is saved first and put back after, so tuning leaves it
+// as it was.  Candidates whose neighbour lists overflow are skipped.
+int batch_tune_persist(lbm_batch *b)
+{
+    const int widths[2] = {128, 64};
+    constexpr int NR = 15;
+    const int rowsc[NR] = {8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 64, 80, 96, 128};
+    constexpr int WARM = 2, TIMED = 8;
+    const int prec = b->precision == LBM_FP64 ? 0 : 1;
+    // save the state
+    size_t total = 0;
+    for (int c = 0; c < b->n; ++c) {
+        const lbm_ctx *x = b->ctx[c];
+        total += x->fbytes + x->gbytes + (size_t)x->N * x->esz + 4 * sizeof(float);
+    }
+    char *save = nullptr;
+    if (cudaMalloc((void **)&save, total) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    const int cur0 = b->ctx[0]->cur;
+    const long long step0 = b->ctx[0]->step;
+    const int diag_every0 = b->diag_every;
+    auto copy_state = [&](bool restore) {
+        size_t o = 0;
+        for (int c = 0; c < b->n; ++c) {
+            const lbm_ctx *x = b->ctx[c];
+            const size_t sb = (size_t)x->N * x->esz;
+            void *live[4] = {x->f[cur0], x->g[cur0], x->S, x->eqs};
+            const size_t len[4] = {x->fbytes, x->gbytes, sb, 4 * sizeof(float)};
+            for (int k = 0; k < 4; ++k) {
+                void *dst = restore ? live[k] : (void *)(save + o);
+                const void *src = restore ? (const void *)(save + o) : live[k];
+                if (cudaMemcpyAsync(dst, src, len[k], cudaMemcpyDeviceToDevice, b->stream) !=
+                    cudaSuccess)
+                    return false;
+                o += len[k];
+            }
+        }
+        return true;
+    };
+    int rc = copy_state(false) ? LBM_OK : LBM_ERR_CUDA;
+    b->diag_every = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = LBM_ERR_CUDA;
+    float best = 3.4e38f;
+    int bw = 0, br = 0;
+    for (int wi = 0; wi < 2 && rc == LBM_OK; ++wi) {
+        int cand[NR + 2], nc = 0;
+        for (int ri = 0; ri < NR; ++ri) cand[nc++] = rowsc[ri];
+        const int per_sm = d2q9_batch_persist_ctas_per_sm(prec, widths[wi], b->seg != 0);
+        const long long slots = (long long)(per_sm > 0 ? per_sm : 4) * b->nsm;
+        for (long long waves = 1; waves <= 2; ++waves)
+            for (int r = 2; r <= 256; r += 2)
+                if (count_tiles(b, widths[wi], r) <= waves * slots) {
+                    bool listed = false;
+                    for (int ri = 0; ri < nc; ++ri) listed = listed || cand[ri] == r;
+                    if (!listed) cand[nc++] = r;
+                    break;
+                }
+        for (int ri = 0; ri < nc && rc == LBM_OK; ++ri) {
+            rc = batch_build_tiles(b, widths[wi], cand[ri]);
+            if (rc || !b->persist_ok) continue;
+            rc = batch_run_persistent(b, WARM);
+            if (rc) break;
+            cudaEventRecord(e0, b->stream);
+            rc = batch_run_persistent(b, TIMED);
+            cudaEventRecord(e1, b->stream);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = LBM_ERR_CUDA;
+                break;
+            }
+            if (*(volatile int *)&b->h_status->err) {  // a wait timed out
+                b->err = LBM_ERR_TIMEOUT;
+                rc = LBM_ERR_TIMEOUT;
+                break;
+            }
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+                best = ms;
+                bw = widths[wi];
+                br = cand[ri];
+            }
+        }
+    }
+    // put the state back (also after a failure: the steps taken are undone)
+    if (!copy_state(true) && rc == LBM_OK) rc = LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess && rc == LBM_OK) rc = LBM_ERR_CUDA;
+    for (int c = 0; c < b->n; ++c) {
+        b->ctx[c]->cur = cur0;
+        b->ctx[c]->step = step0;
+    }
+    b->diag_every = diag_every0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (rc) return rc;
+    if (bw == 0) return LBM_ERR_INVALID_ARG;  // no shape has usable neighbour lists
+    rc = batch_build_tiles(b, bw, br);
+    if (rc == LBM_OK) b->tuned = 1;
+    return rc;
+}
+
 int batch_reset_timeout(lbm_batch *b)
 {
     if (b->err != LBM_ERR_TIMEOUT && !*(volatile int *)&b->h_status->err) return LBM_OK;
@@ -1436,6 +1560,9 @@ int lbm_batch_create(int ncases, const lbm_grid *grids, const lbm_params *params
         }
     }
     b->device = b->ctx[0]->device;
+    b->seg = b->precision != LBM_FP64;
+    for (int c = 0; c < ncases; ++c)
+        if (grids[c].nx % 4 != 0) b->seg = 0;
     BatchCase *h = (BatchCase *)calloc((size_t)ncases, sizeof(BatchCase));
     if (!h) {
         batch_free(b);
@@ -1505,7 +1632,7 @@ int lbm_batch_step(lbm_batch *b, int n)
     if (b->err) return batch_take_err(b);
     if (int rc = batch_ready(b)) return rc;
     if (!b->tuned && n > 0)
-        if (int rc = batch_tune(b)) return rc;
+        if (int rc = b->persist ? batch_tune_persist(b) : batch_tune(b)) return rc;
     if (b->persist && b->persist_ok && n >= 2) return batch_run_persistent(b, n);
     int left = n;
     while (left > 0) {
@@ -1574,7 +1701,7 @@ int lbm_batch_tune(lbm_batch *b, int *width, int *rows)
     if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
     if (int rc = batch_ready(b)) return rc;
     if (int rc = batch_reset_timeout(b)) return rc;
-    if (int rc = batch_tune(b)) return rc;
+    if (int rc = b->persist ? batch_tune_persist(b) : batch_tune(b)) return rc;
     if (width) *width = b->width;
     if (rows) *rows = b->rows;
     return LBM_OK;
@@ -1594,8 +1721,15 @@ int lbm_batch_set_persistent(lbm_batch *b, int on)
 {
     if (!b) return LBM_ERR_INVALID_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
-    if (on && !b->tuned)
-        if (int rc = batch_tune(b)) return rc;
+    if (on && !b->tuned) {
+        // timed on the state when there is one, else with per-step launches
+        if (batch_ready(b) == LBM_OK) {
+            if (int rc = batch_reset_timeout(b)) return rc;
+            if (int rc = batch_tune_persist(b)) return rc;
+        } else if (int rc = batch_tune(b)) {
+            return rc;
+        }
+    }
     if (on && !b->persist_ok) return LBM_ERR_INVALID_ARG;
     b->persist = on ? 1 : 0;
     return LBM_OK;

@@ -172,6 +172,9 @@ struct BatchTile {
 
 // D2Q9 (kernels_d2q9.cu)
 LaunchShape d2q9_shape(int nx, int ny, int num_sms);
+// Shared-memory attributes of the staging multi-step D2Q9 kernels on the
+// current device (dynamic size and carveout).
+cudaError_t d2q9_prepare();
 cudaError_t d2q9_pass(int precision, int pass, const void *params, const PassArgs &a,
                       const LaunchShape &s, cudaStream_t st);
 // one time step of every grid of a batch (strip width 128 or 64); with
@@ -199,16 +202,22 @@ struct PersistArgs {
     int ntiles, ncases, parity0, nsteps;  // nsteps * ntiles < 2^31
     int diag_k;        // step of the launch that carries the diagnostics, or -1
     int *ctr;          // 4 counters, then flags (= ctr + 4): ntiles + 1 step
-                       // counters; all zeroed before the launch
+                       // counters, then case_ctr (= flags + ntiles + 1):
+                       // ncases counters; nctr ints, all zero at the launch
+    int *ctr_next;     // the next launch's set of nctr ints, zeroed by this one
+    int nctr;
     int *flags;
+    int *case_ctr;     // per grid: tiles done with the diagnostics step
     int *err;          // device word set by a wait that timed out (never cleared here)
     int *err_host;     // mapped host word set with it (may be null)
     DiagPartial *partials;  // ntiles
     DiagPartial *records;   // ncases (device-visible; mapped host memory allowed)
 };
-cudaError_t d2q9_batch_persist(int precision, int width, const PersistArgs &pa, int nctas,
-                               cudaStream_t st);
-int d2q9_batch_persist_ctas_per_sm(int precision, int width);
+// seg (FP32): the variant that stages the pulls as row segments, for
+// batches whose grids all have rows of a multiple of 4 nodes.
+cudaError_t d2q9_batch_persist(int precision, int width, bool seg, const PersistArgs &pa,
+                               int nctas, cudaStream_t st);
+int d2q9_batch_persist_ctas_per_sm(int precision, int width, bool seg);
 cudaError_t d2q9_init(int precision, const void *params, const double *phi0, double *mu_tmp,
                       void *f, void *g, void *S, cudaStream_t st);
 cudaError_t d2q9_get_state(int precision, int nx, int ny, const void *f, const void *g,

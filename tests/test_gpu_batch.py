@@ -74,6 +74,37 @@ def test_batch_tuning_keeps_state_and_reports_shape(gpu):
             assert np.array_equal(x, y)
 
 
+def test_multistep_tuning_keeps_state(gpu):
+    """With multi-step launches on, tuning times multi-step launches of the
+    grids' own state and puts the state back: the state, the time and the
+    following steps are those of a batch that was never tuned that way."""
+    cases = ensemble(range(4))
+    runs = []
+    for tune in (False, True):
+        b = gpu.Batch([(sh, prm) for sh, prm, _ in cases], precision="fp32")
+        try:
+            for i, (_, _, phi0) in enumerate(cases):
+                b.case(i).init_phi(phi0)
+            b.set_shape(128, 16)
+            b.set_persistent(True)
+            b.step(5)
+            before = [b.case(i).get_state() for i in range(len(b))]
+            if tune:
+                w, r = b.tune()
+                assert w in (64, 128) and r >= 2 and r % 2 == 0
+                for i in range(len(b)):
+                    for x, y in zip(before[i], b.case(i).get_state()):
+                        assert np.array_equal(x, y)
+                    assert b.case(i).t == 5
+            b.step(7)
+            runs.append([b.case(i).get_state() for i in range(len(b))])
+        finally:
+            b.close()
+    for sa, sb in zip(*runs):
+        for x, y in zip(sa, sb):
+            assert np.array_equal(x, y)
+
+
 def test_batch_requires_lockstep(gpu):
     from paper_2311_10827_gb300 import capi
     cases = ensemble(range(3))

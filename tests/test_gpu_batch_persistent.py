@@ -90,13 +90,15 @@ def test_multistep_equals_per_step_bench_config(gpu):
 def test_multistep_walks_more_tiles_than_resident_ctas(gpu):
     """64 grids of the ensemble recipe (seeds 0..63: N from U{64..512}, uneven
     sizes) at 128 x 28 and 64 x 8 tiles: thousands of tiles, several per
-    resident CTA, walked as a queue every step."""
+    resident CTA, walked as a queue every step.  Hundreds of steps: a CTA
+    whose warps disagreed on their next pair (a race on the ticket) showed
+    only after about a hundred steps of this batch."""
     cases = []
     for seed in range(64):
         c = wl.ensemble_case(seed)
         cases.append(((c["n"], c["n"]), dict(BASE, rho_l=c["rho_ratio"]),
                       wl.droplet(c["n"], c["n"], c["R"], 4.0)))
-    assert_same(run_pair(gpu, cases, "fp32", 128, 28, (3, 30)))
+    assert_same(run_pair(gpu, cases, "fp32", 128, 28, (3, 30, 300)))
     small = cases[:16]
     assert_same(run_pair(gpu, small, "fp64", 64, 8, (5, 2)))
 
