@@ -108,16 +108,54 @@ __device__ __forceinline__ void pull9(const T *__restrict__ s, unsigned N, unsig
     v[8] = ldp<NC>(s + (8u * N + rp + xm));  // c = (1,-1)
 }
 
-// A 16-byte asynchronous copy global -> shared that reads L2 only
-// (cp.async.cg: no L1 allocation), and its group fences: a thread's own
-// copies are visible to it after wait_group, to the CTA after a barrier.
-__device__ __forceinline__ void cp16(float *dst, const float *src)
+// Bulk asynchronous copies global -> shared (the copy engine; 16-byte
+// aligned addresses, sizes a multiple of 16 bytes) completing on an
+// mbarrier: the barrier's phase completes once its one expected arrival
+// has come and every byte it was told to expect has landed.
+__device__ __forceinline__ unsigned smem_u32(const void *p)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(float *dst, const float *src, unsigned bytes,
+                                         unsigned long long *b)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b))
+        : "memory");
+}
+// Orders this thread's earlier view of global memory (what it acquired from
+// other CTAs' ordinary stores) before its later copy-engine reads.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Longest wait for a stage's bulk copies, in SM clock cycles (about 1 s).
+constexpr long long STAGE_WAIT_CYCLES = 2000000000LL;
 
 // The paired FP32 datapath (add/mul/fma.rn.f32x2): two independent lanes per
 // instruction, each rounding exactly as the scalar instruction would.  The
@@ -185,7 +223,9 @@ struct TileSmem {
     T phs[R * WP];
     T mus[R * WM];
     double red[7][NT / 32];
+    unsigned long long bar[2];  // the stages' mbarriers (bulk-copy staging)
     int bad;
+    int stage_timeout;          // a stage's wait gave up (set, never cleared here)
 };
 
 // Row-segment staging of the pulls (FP32, rows of a multiple of 4 nodes).
@@ -195,10 +235,10 @@ struct TileSmem {
 // updated.  An f or g segment is the source row of its population (the row
 // shifted by -c_y) over columns x0 - 4 .. x0 + TX + 3, so that a thread's pull
 // from x - c_x is element tx + 4 - c_x; the S segment spans x0 .. x0 + TX - 1.
-// The segments are copied in 16-byte chunks with cp.async.cg, which reads L2
-// only (no L1 allocation), so the same staging is valid in launches whose
-// other CTAs wrote the source rows earlier in the launch.  Two stages: the
-// copies for the next iteration fly while this one computes.
+// Each segment is one bulk asynchronous copy (two where it wraps the
+// periodic seam), which the copy engine reads from L2, completing on the
+// stage's mbarrier.  Two stages: the copies for the next iteration fly
+// while this one computes.
 template <int TX>
 struct SegLayout {
     static constexpr int W = TX + 8;                      // elements per f / g segment
@@ -253,12 +293,13 @@ constexpr unsigned cy_packed()
     return v | (1u << 18);
 }
 
-// Whether a grid's pulls can be staged in 16-byte chunks: FP32 storage,
-// rows of a multiple of 4 nodes and 16-byte aligned buffers.
-template <typename T>
+// Whether a grid's pulls can be staged by tiles of width TX: FP32 storage,
+// rows of a multiple of 4 nodes and at least TX + 8 nodes (a segment then
+// wraps the periodic seam at most once), 16-byte aligned buffers.
+template <typename T, int TX>
 __device__ __forceinline__ bool seg_ok(int nx, const void *f, const void *g, const void *S)
 {
-    return sizeof(T) == 4 && (nx & 3) == 0 &&
+    return sizeof(T) == 4 && (nx & 3) == 0 && nx >= TX + 8 &&
            (((unsigned long long)f | (unsigned long long)g | (unsigned long long)S) & 15) == 0;
 }
 
@@ -266,13 +307,15 @@ __device__ __forceinline__ bool seg_ok(int nx, const void *f, const void *g, con
 // dir (+1 down from y0, -1 up from yend - 1); diagnostics partial record
 // `part` (PASS_DIAG).  Shared by the single-grid and the batched kernels.
 // dyn is the kernel's dynamic shared memory (tile_dyn_bytes).  SEG: the pulls
-// are staged as row segments (FP32; seg_ok must hold); else each thread
+// are staged as row segments (FP32; seg_ok must hold) by bulk copies on the
+// stages' mbarriers (sm.bar, initialised by the kernel; bph holds the parity
+// each stage waits for next, carried from tile to tile); else each thread
 // loads its own pulls into registers, through the read-only path (NC: data
 // constant for the launch) or from L2 only (multi-step launches).
 template <typename T, int TX, int PASS, bool NC = true, bool SEG = false>
 __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const StepParams<T> &P,
                                           const PassArgs &a, int x0, int y0, int yend, int dir,
-                                          int part)
+                                          int part, unsigned &bph)
 {
     using SM = TileSmem<T, TX>;
     using SL = SegLayout<TX>;
@@ -344,59 +387,86 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const Ste
         }
     };
 
-    // Staged pulls.  Warp w copies segments w*SPW.., (w+NW)*SPW.., ... of the
-    // stage; lane l (within its segment) the main chunk l (columns x0 + 4l..)
-    // and lanes 0 / 1 also the left / right halo chunk.  Chunks never straddle
-    // the periodic seam (nx % 4 == 0).
-    const int lane = lin & 31, wid = lin >> 5;
-    const int l4 = lane % SL::LPS, sub = lane / SL::LPS;
-    const unsigned cMain = SEG ? (unsigned)wrapi(x0 + 4 * l4, nx) : 0u;
-    const unsigned cHalo = SEG ? (unsigned)wrapi(l4 == 0 ? x0 - 4 : x0 + TX, nx) : 0u;
-    const int eHalo = l4 == 0 ? 0 : TX + 4;
-    const bool haloL = l4 < 2;
     // where the f segments of stage st go and where its g segments go
     auto fbuf = [&](int st) { return stg + (DSEG ? 0 : st * SL::STAGE); };
     auto gbuf = [&](int st) {
         return stg + (DSEG ? SL::DG + st * TYB * SL::NG * SL::W : st * SL::STAGE + SL::GOFF);
     };
-    // if doF, the f segments of phi rows mF.. (march coordinates); if doG, the
-    // g (and S) segments of rows mG.. (only rows of the tile); stage st
-    auto issue_stage = [&](int st, bool doF, int mF, bool doG, int mG) {
+    // Bulk staging: one thread arrives on the stage's mbarrier expecting the
+    // stage's bytes (before a barrier that precedes the copies), then the
+    // thread (ty, 32 + r), r < 20, copies segment r of thread row ty as one
+    // bulk copy (two where it wraps the periodic seam) completing on that
+    // mbarrier.  Those threads sit in warps without halo work (the phi and mu
+    // halo columns belong to threads tx < 4), so the copies do not lengthen
+    // the busiest warp.
+    constexpr int NSR = SL::NF + SL::NG + 1;  // segments per thread row
+    const int rseg = tx - 32;
+    auto bulk_expect = [&](int st, int mG, bool doG) {
+        if (lin == 32) {
+            int rowsG = 0;
+#pragma unroll
+            for (int j = 0; j < TYB; ++j) rowsG += (doG && mG + j < nout) ? 1 : 0;
+            const unsigned bytes = (unsigned)((TYB * SL::NF + rowsG * SL::NG) * SL::W) * 4u +
+                                   (STAGE_S ? (unsigned)(rowsG * TX) * 4u : 0u);
+            mbar_arrive_expect_tx(&sm.bar[st], bytes);
+        }
+    };
+    auto bulk_copy = [&](int st, int mF, int mG, bool doG) {
         float *const sb = stg + st * SL::STAGE;
-        const float *const fs = reinterpret_cast<const float *>(fsrc);
-        const float *const gs = reinterpret_cast<const float *>(gsrc);
-        const float *const ss = static_cast<const float *>(a.S);
-        for (int grp = wid; grp * SL::SPW < SL::NSEG; grp += NW) {
-            const int s = grp * SL::SPW + sub;
-            const int j = s / (SL::NF + SL::NG + 1), r = s - j * (SL::NF + SL::NG + 1);
+        unsigned long long *const bar = &sm.bar[st];
+        if (rseg >= 0 && rseg < NSR) {
+            const int j = ty, r = rseg;
             const float *src;
             float *dst;
-            int m;
-            bool halo = true;
+            int m, u0, len;
             if (r < SL::NF) {
-                if (!doF) continue;
                 m = mF + j;
-                src = fs + (unsigned)r * N;
+                src = reinterpret_cast<const float *>(fsrc) + (unsigned)r * N;
                 dst = fbuf(st) + (j * SL::NF + r) * SL::W;
+                u0 = x0 - 4;
+                len = SL::W;
             } else if (r < SL::NF + SL::NG) {
                 m = mG + j;
-                if (!doG || m >= nout) continue;
-                src = gs + (unsigned)(r - SL::NF) * N;
+                src = reinterpret_cast<const float *>(gsrc) + (unsigned)(r - SL::NF) * N;
                 dst = gbuf(st) + (j * SL::NG + r - SL::NF) * SL::W;
+                u0 = x0 - 4;
+                len = SL::W;
             } else {
                 m = mG + j;
-                if (!doG || !STAGE_S || m >= nout) continue;
-                src = ss;
-                dst = sb + SL::SOFF + j * TX - 4;
-                halo = false;
+                src = static_cast<const float *>(a.S);
+                dst = sb + SL::SOFF + j * TX;
+                u0 = x0;
+                len = TX;
             }
-            const int pop = r < SL::NF ? r : r - SL::NF;
-            const int cy = r < SL::NF + SL::NG ? (int)((cy_packed() >> (2 * pop)) & 3u) - 1 : 0;
-            const unsigned ro = (unsigned)wrap_row(first + dir * m - cy, ny, small) * nx;
-            cp16(dst + 4 + 4 * l4, src + ro + cMain);
-            if (halo && haloL) cp16(dst + eHalo, src + ro + cHalo);
+            const bool go = r < SL::NF || (doG && m < nout && (r < SL::NF + SL::NG || STAGE_S));
+            if (go) {
+                const int pop = r < SL::NF ? r : r - SL::NF;
+                const int cy =
+                    r < SL::NF + SL::NG ? (int)((cy_packed() >> (2 * pop)) & 3u) - 1 : 0;
+                const float *const row =
+                    src + (unsigned)wrap_row(first + dir * m - cy, ny, small) * nx;
+                // columns u0 .. u0 + len - 1, wrapped: at most one seam (nx >= TX + 8)
+                const int c0 = u0 < 0 ? u0 + nx : u0;
+                const int n1 = len < nx - c0 ? len : nx - c0;
+                bulk_g2s(dst, row + c0, (unsigned)n1 * 4u, bar);
+                if (n1 < len) bulk_g2s(dst + n1, row, (unsigned)(len - n1) * 4u, bar);
+            }
         }
-        cp_commit();
+    };
+    // wait until stage st's bulk copies have landed (bounded: on a timeout
+    // the tile records it in sm.stage_timeout and goes on)
+    auto wait_stage = [&](int st) {
+        const unsigned par = (bph >> st) & 1u;
+        if (!mbar_try_wait(&sm.bar[st], par)) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&sm.bar[st], par)) {
+                if (clock64() - t0 > STAGE_WAIT_CYCLES) {
+                    sm.stage_timeout = 1;
+                    break;
+                }
+            }
+        }
+        bph ^= 1u << st;
     };
     // phi row from stage st (thread row ty), keeping the own pulls
     auto phi_row_seg = [&](int sl, int st, T v[9], T &lo) {
@@ -450,26 +520,35 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const Ste
     T fcur[9], fnext[9], locur = T(0), lonext = T(0);
     if constexpr (DSEG) {
         // one f buffer: the two phi row pairs one after the other
-        issue_stage(0, true, -2, false, 0);
-        cp_wait_all();
+        if (rseg >= 0 && rseg < NSR) fence_proxy_async_global();
+        bulk_expect(1, 0, false);
         __syncthreads();
-        phi_row_seg(slot(first + dir * (ty - 2)), 0, fnext, lonext);
-        __syncthreads();
-        issue_stage(0, true, 0, false, 0);
-        cp_wait_all();
-        __syncthreads();
+        bulk_copy(1, -2, 0, false);
+        wait_stage(1);
+        phi_row_seg(slot(first + dir * (ty - 2)), 1, fnext, lonext);
+        bulk_expect(0, 0, false);
+        __syncthreads();  // the f buffer is read before it is refilled
+        bulk_copy(0, 0, 0, false);
+        wait_stage(0);
         phi_row_seg(slot(first + dir * ty), 0, fcur, locur);
+        bulk_expect(0, 0, true);
         __syncthreads();
-        issue_stage(0, true, 2, true, 0);
+        bulk_copy(0, 2, 0, true);
     } else if constexpr (SEG) {
-        issue_stage(1, true, -2, false, 0);
-        issue_stage(0, true, 0, false, 0);
-        cp_wait_all();
+        // the acquired view of the other tiles' stores precedes the copies
+        if (rseg >= 0 && rseg < NSR) fence_proxy_async_global();
+        bulk_expect(1, 0, false);
+        bulk_expect(0, 0, false);
         __syncthreads();
+        bulk_copy(1, -2, 0, false);
+        bulk_copy(0, 0, 0, false);
+        wait_stage(1);
+        wait_stage(0);
         phi_row_seg(slot(first + dir * (ty - 2)), 1, fnext, lonext);
         phi_row_seg(slot(first + dir * ty), 0, fcur, locur);
+        bulk_expect(0, 0, true);
         __syncthreads();  // stage 0 is read before it is refilled
-        issue_stage(0, true, 2, true, 0);
+        bulk_copy(0, 2, 0, true);
     } else {
         phi_row(first + dir * (ty - 2), slot(first + dir * (ty - 2)), fnext, lonext);
         phi_row(first + dir * ty, slot(first + dir * ty), fcur, locur);
@@ -496,17 +575,15 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const Ste
         T Sprev = T(0);
         const unsigned nrow = (unsigned)wrap_row(row, ny, small) * nx;
         if constexpr (SEG) {
-            // this iteration's stage has landed (own copies) and is visible
-            // (barrier); every read of the other stage (the previous
-            // iteration) is done, so it is refilled for the next iteration
-            // (a diagnostics step refills its one f buffer after the phi rows
-            // are read, below)
-            cp_wait_all();
-            __syncthreads();
-            if (t + TYB < nout) issue_stage(st ^ 1, !DSEG, t + TYB + 2, true, t + TYB);
+            // this iteration's stage has landed (the other stage, and a
+            // diagnostics step's one f buffer, are refilled after the barrier
+            // below, once every read of them by this iteration's phi rows and
+            // the previous iteration is done)
+            wait_stage(st);
             if (DSEG && NEED_S && out_ok)
                 Sprev = __ldcg(static_cast<const T *>(a.S) + (nrow + xo));  // from L2
             phi_row_seg(ring(2 + ty), st, fnext, lonext);
+            if (t + TYB < nout) bulk_expect(st ^ 1, t + TYB, true);
         } else {
             // issue the loads of the own node first so they overlap the stencil work
             const unsigned rm = (unsigned)wrap_row(row - 1, ny, small) * nx;
@@ -518,7 +595,7 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const Ste
             phi_row(first + dir * (t + 2 + ty), ring(2 + ty), fnext, lonext);
         }
         __syncthreads();
-        if (DSEG && t + TYB < nout) issue_stage(0, true, t + TYB + 2, false, 0);
+        if (SEG && t + TYB < nout) bulk_copy(st ^ 1, t + TYB + 2, t + TYB, true);
         mu_row(ring(1 + ty - dir), ring(1 + ty), ring(1 + ty + dir));
         __syncthreads();
 
@@ -774,7 +851,6 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const Ste
         for (int i = 0; i < 9; ++i) fcur[i] = fnext[i];
         locur = lonext;
     }
-    if (SEG) cp_wait_all();  // nothing in flight when the tile ends
 
     if (PASS & PASS_DIAG) {
         __syncthreads();  // every flag write of the march is done
@@ -793,6 +869,7 @@ __device__ __forceinline__ void d2q9_tile(TileSmem<T, TX> &sm, T *dyn, const Ste
           d_bad = *dbad ? T(1) : T(0);
         warp_reduce(d_phi, d_E, d_u2, d_mumin, d_mumax, d_bud, d_bad);
         double(*red)[NW] = sm.red;
+        const int lane = lin & 31, wid = lin >> 5;
         if (lane == 0) {
             red[0][wid] = d_phi;
             red[1][wid] = d_E;
@@ -841,8 +918,9 @@ __global__ void __launch_bounds__((Occ<T, PASS, TX>::nth), (Occ<T, PASS, TX>::ct
     // reversed on every other step
     const int dir = ((blockIdx.y & 1) ? -1 : 1) * (a.flip ? -1 : 1);
     __shared__ TileSmem<T, TX> sm;
+    unsigned bph = 0;  // no bulk staging here
     d2q9_tile<T, TX, PASS>(sm, reinterpret_cast<T *>(tile_dyn), P, a, blockIdx.x * TX, y0,
-                           min(y0 + rows, P.ny), dir, blockIdx.y * gridDim.x + blockIdx.x);
+                           min(y0 + rows, P.ny), dir, blockIdx.y * gridDim.x + blockIdx.x, bph);
 }
 
 // Batched: CTA k runs tile k of a flat tile table over many independent grids
@@ -870,8 +948,9 @@ __global__ void __launch_bounds__((Occ<T, PASS, TX>::nth), (Occ<T, PASS, TX>::ct
     a.eqs_dst = c.eqs + (parity ^ 1);
     a.eqs_target = c.eqs + 2;
     __shared__ TileSmem<T, TX> sm;
+    unsigned bph = 0;  // no bulk staging here
     d2q9_tile<T, TX, PASS>(sm, reinterpret_cast<T *>(tile_dyn), P, a, t.x0, t.y0, t.yend,
-                           parity ? -t.dir : t.dir, blockIdx.x);
+                           parity ? -t.dir : t.dir, blockIdx.x, bph);
 }
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p)
@@ -1002,13 +1081,15 @@ __global__ void __launch_bounds__(RG) d2q9_batch_reduce_kernel(const DiagPartial
 // the staging CTAs need.
 //
 // Memory ordering of the pulls.  Every population, S and phi value that
-// other tiles write during the launch is read from L2 only: by the 16-byte
-// row-segment copies (cp.async.cg) or, on the register path, by
-// ld.global.cg.  The writer CTA stores, passes bar.sync, and its thread 0
+// other tiles write during the launch is read from L2 only: by the bulk
+// row-segment copies (the copy engine reads L2) or, on the register path,
+// by ld.global.cg.  The writer CTA stores, passes bar.sync, and its thread 0
 // fences and does st.release.gpu on the tile's counter; a polling lane of
 // the reader does ld.acquire.gpu, observes the count, fences, and the CTA
-// passes bar.sync before any copy or load of the next step is issued.  No
-// read of this launch's data goes through L1.
+// passes bar.sync before any copy or load of the next step is issued; a
+// thread that issues bulk copies first executes fence.proxy.async.global,
+// which orders what it has observed through ordinary loads before its
+// copy-engine reads.  No read of this launch's data goes through L1.
 //
 // FP32 equilibrium shift: the source buffer's shift is the stored one at
 // step 0 and the target after it (what step 0 wrote with); the target is
@@ -1044,7 +1125,31 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
     // pair it - 2 was read by every thread before the barriers of pair it - 1
     __shared__ int s_next[2], s_abort, s_diag, s_stop;
     int it = 0;
+    // a tile whose state is invalid: NaN in its rest population of both
+    // buffers (so phi, whichever buffer is current) and in S
+    auto poison = [&](const BatchCase &c, const BatchTile &t, const StepParams<T> &P) {
+        T *S = static_cast<T *>(c.S);
+        T *f0 = static_cast<T *>(c.f[0]), *f1 = static_cast<T *>(c.f[1]);
+        for (int x = t.x0 + threadIdx.x; x < t.x0 + TX && x < P.nx; x += blockDim.x)
+            for (int y = t.y0 + (int)threadIdx.y; y < t.yend; y += TYB) {
+                const size_t n = (size_t)y * P.nx + x;
+                S[n] = T(NAN);
+                f0[n] = T(NAN);
+                f1[n] = T(NAN);
+            }
+    };
     __shared__ TileSmem<T, TX> sm;
+    // the stages' mbarriers (bulk-copy staging), their next parities
+    unsigned bph = 0;
+    if (SEGK) {
+        if (lin == 0) {
+            mbar_init(&sm.bar[0], 1);
+            mbar_init(&sm.bar[1], 1);
+            sm.stage_timeout = 0;
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
     int tk = blockIdx.x;
     while (tk < total) {
         const int k = tk / pa.ntiles, ti = tk - k * pa.ntiles;
@@ -1089,17 +1194,7 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
             }
             __syncthreads();
             if (s_abort) {
-                // the tile's state is invalid: NaN in its rest population of
-                // both buffers (so phi, whichever buffer is current) and in S
-                T *S = static_cast<T *>(c.S);
-                T *f0 = static_cast<T *>(c.f[0]), *f1 = static_cast<T *>(c.f[1]);
-                for (int x = t.x0 + threadIdx.x; x < t.x0 + TX && x < P.nx; x += blockDim.x)
-                    for (int y = t.y0 + (int)threadIdx.y; y < t.yend; y += TYB) {
-                        const size_t n = (size_t)y * P.nx + x;
-                        S[n] = T(NAN);
-                        f0[n] = T(NAN);
-                        f1[n] = T(NAN);
-                    }
+                poison(c, t, P);
                 return;
             }
         }
@@ -1120,20 +1215,34 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
         a.flip = 0;
         const int dir = parity ? -t.dir : t.dir;
         T *const dyn = reinterpret_cast<T *>(tile_dyn);
-        const bool seg = SEGK && seg_ok<T>(P.nx, a.f_src, a.g_src, a.S);
+        const bool seg = SEGK && seg_ok<T, TX>(P.nx, a.f_src, a.g_src, a.S);
         if (k == pa.diag_k) {
             if (seg)
                 d2q9_tile<T, TX, PASS_STATE | PASS_DIAG, false, SEGK>(sm, dyn, P, a, t.x0, t.y0,
-                                                                       t.yend, dir, ti);
+                                                                       t.yend, dir, ti, bph);
             else
                 d2q9_tile<T, TX, PASS_STATE | PASS_DIAG, false>(sm, dyn, P, a, t.x0, t.y0, t.yend,
-                                                                 dir, ti);
+                                                                 dir, ti, bph);
         } else if (seg) {
-            d2q9_tile<T, TX, PASS_STATE, false, SEGK>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti);
+            d2q9_tile<T, TX, PASS_STATE, false, SEGK>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti,
+                                                      bph);
         } else {
-            d2q9_tile<T, TX, PASS_STATE, false>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti);
+            d2q9_tile<T, TX, PASS_STATE, false>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti, bph);
         }
         __syncthreads();  // every output of the step (and its partial) is stored
+        if (SEGK && sm.stage_timeout) {
+            // a stage's copies did not land in time: the tile is invalid; the
+            // error word stops the other CTAs
+            if (lin == 0) {
+                atomicExch(pa.err, 1);
+                if (pa.err_host) {
+                    *(volatile int *)pa.err_host = 1;
+                    __threadfence_system();
+                }
+            }
+            poison(c, t, P);
+            return;
+        }
         // counters of the launch's last steps (one atomic per tile each):
         // the last tile of a grid in the diagnostics step reduces that grid's
         // partials (ctr[3] counts the grids reduced); the last tile of the

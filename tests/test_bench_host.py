@@ -57,10 +57,10 @@ def test_committed_traffic_records_match_the_kernel_source():
         assert os.path.exists(path), path
         assert bench.ncu_traffic(mode) is not None, (mode, "re-capture the DRAM traffic")
         # the recorded bytes are close to the algorithmic 2 x 1024^2 x 152 B per
-        # step: plus the rest population's low word (8 B, 1.05x) and, for the
-        # staged multi-step kernel at 64 x 16 tiles, the halo rows and columns
-        # that neighbouring tiles both read and L2 does not always serve
-        # (1.16x measured); far above that would mean wasted re-reads
+        # step: plus the rest population's low word (8 B, 1.05x) and the halo
+        # rows and columns that neighbouring tiles both read, when L2 does not
+        # serve them (1.07x to 1.16x measured for the staged multi-step
+        # kernel at 64 x 16 tiles); far above that would mean wasted re-reads
         assert 0.8 < bench.ncu_traffic(mode) / (2 * 1024 * 1024 * 152) < 1.2
 
 

@@ -1,12 +1,15 @@
 """The default bench line's kernel against the FP64 oracle directly, at the
-bench's tile shape (128-column strips, 28-row tiles: 14 two-row march
+tile shapes the bench runs: 64 x 16 (what the multi-step tuner picks for the
+1024^2 pair: the staged multi-step kernel walks more tiles than resident
+CTAs as a queue) and 128 x 28 (one tile per CTA; 14 two-row march
 iterations per tile, so the phi/mu rings wrap and the two-stage copy
 pipeline advances many times), on the bench's configuration scaled down:
 two droplet grids (density ratios 10 and 100, viscosity ratio 10, W = 4,
-sigma = 1e-3, M = 0.05) of 384 x 150 nodes (three strips; five full row
-tiles and a ragged 10-row one), FP32, both launch forms (one multi-step
-launch per call, and per-step launches), with the FP64 diagnostics fused
-every 20 steps as in the bench.
+sigma = 1e-3, M = 0.05) of 384 x 150 nodes (rows a multiple of 4 nodes, so
+multi-step launches stage their pulls; ragged last row tiles of 6 and 10
+rows), FP32, both launch forms (one multi-step launch per call, and
+per-step launches), with the FP64 diagnostics fused every 20 steps as in
+the bench (the diagnostics steps run the staged layout of their own).
 
 * one step from a perturbed state that FP32 holds exactly (so both sides
   start from the same numbers): phi within 1e-5 and u within 1e-6;
@@ -59,18 +62,22 @@ def oracle_long(oracle_mod):
         return pool.map(_oracle_run, [(r, STEPS) for r in RATIOS])
 
 
-def _batch(sim, persistent):
+FORMS = [(True, (64, 16)), (True, (128, 28)), (False, (128, 28))]
+IDS = ["multistep-64x16", "multistep-128x28", "perstep-128x28"]
+
+
+def _batch(sim, persistent, tile):
     b = sim.Batch([(SHAPE, dict(BASE, rho_l=r)) for r in RATIOS], precision="fp32")
-    b.set_shape(128, 28)
+    b.set_shape(*tile)
     if persistent:
         b.set_persistent(True)
     b.set_diag_every(20)
     return b
 
 
-@pytest.mark.parametrize("persistent", [True, False])
-def test_headline_kernel_one_step_from_perturbed_state(gpu, oracle_mod, persistent):
-    b = _batch(gpu, persistent)
+@pytest.mark.parametrize("persistent,tile", FORMS, ids=IDS)
+def test_headline_kernel_one_step_from_perturbed_state(gpu, oracle_mod, persistent, tile):
+    b = _batch(gpu, persistent, tile)
     try:
         states = []
         for i, r in enumerate(RATIOS):
@@ -95,9 +102,9 @@ def test_headline_kernel_one_step_from_perturbed_state(gpu, oracle_mod, persiste
         b.close()
 
 
-@pytest.mark.parametrize("persistent", [True, False])
-def test_headline_kernel_2000_steps_against_oracle(gpu, oracle_long, persistent):
-    b = _batch(gpu, persistent)
+@pytest.mark.parametrize("persistent,tile", FORMS, ids=IDS)
+def test_headline_kernel_2000_steps_against_oracle(gpu, oracle_long, persistent, tile):
+    b = _batch(gpu, persistent, tile)
     try:
         for i in range(len(b)):
             b.case(i).init_phi(_phi0())
