@@ -594,13 +594,17 @@ def run_native(args, rank, world, local_rank):
 DIAG_RECORD_BYTES = 64  # one FP64 record per grid: 8 doubles on the device
 
 
+STEP_CAP = 1024  # steps per multi-step launch (the library splits longer calls)
+
+
 def launches_multi_step(t0, k, de):
     """Kernel launches of one multi-step lbm_batch_step(k) call starting at
     time t0 with diagnostics every de steps: the launch is split so that it
-    holds at most one diagnostics step (the library's rule)."""
+    holds at most STEP_CAP steps and at most one diagnostics step (the
+    library's rules)."""
     count, t, left = 0, t0, k
     while left > 0:
-        m = left
+        m = min(left, STEP_CAP)
         d = (t + de - 1) // de * de
         if d < t + m and d + de < t + m:
             m = d + de - t

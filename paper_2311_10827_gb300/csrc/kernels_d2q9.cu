@@ -1119,11 +1119,18 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
     // the next launch's counters (this launch uses the other set)
     for (int i = blockIdx.x * NTH + lin; i < pa.nctr; i += gridDim.x * NTH) pa.ctr_next[i] = 0;
     if (fixed && (int)blockIdx.x >= pa.ntiles) return;
-    // s_next is double-buffered by the CTA's pair count: thread 0 writes the
-    // slot of pair it at the top of pair it, before any barrier, while the
-    // other warps may still be reading the slot of pair it - 1; the slot of
-    // pair it - 2 was read by every thread before the barriers of pair it - 1
-    __shared__ int s_next[2], s_abort, s_diag, s_stop;
+    // s_next and s_stop (the next pair, the error word) are written by thread
+    // 0 before the barrier that ends a pair and read after it; they are
+    // double-buffered by the CTA's pair count, so that a slot is written again
+    // only after every thread has passed the barriers of the pair between
+    __shared__ int s_next[2], s_stop[2], s_abort, s_diag;
+    // s_stepdone: every tile has finished the steps before this one.  It is
+    // read by every thread at the top of a pair and written only by thread 0
+    // between the two barriers that end a pair; lane 31 of the waiting warp
+    // records what it observed in s_seen, which thread 0 folds in there.
+    __shared__ int s_stepdone, s_seen;
+    if (lin == 0) s_stepdone = s_seen = 0;
+    __syncthreads();
     int it = 0;
     // a tile whose state is invalid: NaN in its rest population of both
     // buffers (so phi, whichever buffer is current) and in S
@@ -1155,19 +1162,24 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
         const int k = tk / pa.ntiles, ti = tk - k * pa.ntiles;
         // the next pair (queue) and the error word are fetched now and used
         // after the tile, so that neither round trip delays it
-        int err_seen = 0;
+        int tk_next = 0, err_seen = 0;  // thread 0's, kept in registers until the tile ends
         if (lin == 0) {
-            if (!fixed) s_next[it & 1] = atomicAdd(pa.ctr, 1) + (int)gridDim.x;
+            if (!fixed) tk_next = atomicAdd(pa.ctr, 1) + (int)gridDim.x;
             err_seen = ld_relaxed_gpu(pa.err);
         }
         const BatchTile t = pa.tiles[ti];
         const BatchCase &c = pa.cases[t.c];
         const StepParams<T> P = *reinterpret_cast<const StepParams<T> *>(
             sizeof(T) == 4 ? (const void *)&c.pf : (const void *)&c.pd);
-        if (k > 0) {
+        // Before step k > 0 of a tile: once this CTA has seen every tile finish
+        // step k - 1 (the step's completion count, acquired), no wait is
+        // needed; else lane 31 reads that count while the other lanes wait
+        // for the tile and its neighbours.
+        if (k > 0 && !(s_stepdone >= k && ti != pa.stall_tile)) {
             if (lin < 32) {
                 const int *nb = pa.nbr + (size_t)ti * (PERSIST_NBMAX + 1);
                 bool bad = false;
+                if (lin == 31 && ld_acquire_gpu(pa.step_done + (k - 1)) == pa.ntiles) s_seen = k;
                 if (lin <= nb[0]) {  // lane 0: the tile itself; lanes 1..: its neighbours
                     const int *fl = pa.flags + (lin == 0 ? ti : nb[lin]);
                     const long long t0 = clock64();
@@ -1229,6 +1241,14 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
         } else {
             d2q9_tile<T, TX, PASS_STATE, false>(sm, dyn, P, a, t.x0, t.y0, t.yend, dir, ti, bph);
         }
+        // every thread read s_stepdone at this pair's top, before the tile's
+        // barriers: thread 0 folds in what lane 31 saw, for the next pair, and
+        // publishes the next pair and the error word it fetched
+        if (lin == 0) {
+            if (s_seen > s_stepdone) s_stepdone = s_seen;
+            s_next[it & 1] = tk_next;
+            s_stop[it & 1] = err_seen;
+        }
         __syncthreads();  // every output of the step (and its partial) is stored
         if (SEGK && sm.stage_timeout) {
             // a stage's copies did not land in time: the tile is invalid; the
@@ -1243,26 +1263,33 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
             poison(c, t, P);
             return;
         }
-        // counters of the launch's last steps (one atomic per tile each):
-        // the last tile of a grid in the diagnostics step reduces that grid's
+        const int next = fixed ? tk + pa.ntiles : s_next[it & 1];
+        const int stop = s_stop[it & 1];
+        ++it;
+        // Thread 0 publishes the tile's step (release) and counts it, and the
+        // CTA waits for it before the next pair (letting the other warps run
+        // ahead into the next tile's copies made a step 27% slower).  The
+        // counters of the launch's last steps (one atomic per tile each): the
+        // last tile of a grid in the diagnostics step reduces that grid's
         // partials (ctr[3] counts the grids reduced); the last tile of the
         // final step (then every pair is done) records the final shift, after
-        // every reduction
+        // every reduction.
+        const bool last_steps = k == pa.diag_k || k == pa.nsteps - 1;
         if (lin == 0) {
             __threadfence();
             st_release_gpu(pa.flags + ti, k + 1);
-            int fl = 0;
-            if (k == pa.diag_k &&
-                atomicAdd(pa.case_ctr + t.c, 1) == pa.tile0[t.c + 1] - pa.tile0[t.c] - 1)
-                fl |= 1;
-            if (k == pa.nsteps - 1 && atomicAdd(pa.ctr + 2, 1) == pa.ntiles - 1) fl |= 2;
-            s_diag = fl;
-            s_stop = err_seen;
+            atomicAdd(pa.step_done + k, 1);  // the step's completion count
+            if (last_steps) {
+                int fl = 0;
+                if (k == pa.diag_k &&
+                    atomicAdd(pa.case_ctr + t.c, 1) == pa.tile0[t.c + 1] - pa.tile0[t.c] - 1)
+                    fl |= 1;
+                if (k == pa.nsteps - 1 && atomicAdd(pa.ctr + 2, 1) == pa.ntiles - 1) fl |= 2;
+                s_diag = fl;
+            }
         }
         __syncthreads();
-        const int next = fixed ? tk + pa.ntiles : s_next[it & 1];
-        ++it;
-        const int fl = s_diag, stop = s_stop;
+        const int fl = last_steps ? s_diag : 0;
         if (fl & 1) {  // every partial of this grid's diagnostics step is written
             __threadfence();
             reduce_case(pa.partials, pa.tile0[t.c], pa.tile0[t.c + 1], pa.cases[t.c],
@@ -1508,7 +1535,8 @@ cudaError_t d2q9_batch_persist(int precision, int width, bool seg, const Persist
                                int nctas, cudaStream_t st)
 {
     if (pa.flags != pa.ctr + 4 || pa.case_ctr != pa.flags + pa.ntiles + 1 ||
-        pa.nctr != pa.ntiles + 5 + pa.ncases)
+        pa.step_done != pa.case_ctr + pa.ncases ||
+        pa.nctr != pa.ntiles + 5 + pa.ncases + PERSIST_STEP_CAP || pa.nsteps > PERSIST_STEP_CAP)
         return cudaErrorInvalidValue;
     if (precision == 0)
         return width == 64 ? launch_persist_t<double, 64, false>(pa, nctas, st)

@@ -955,9 +955,11 @@ struct lbm_batch {
                      // multi-step launches stage their pulls as row segments
     int *d_nbr;      // per tile: count, then up to PERSIST_NBMAX neighbour tiles
     int *d_ctr;      // two sets, used by alternate launches, each: 4 counters, per tile
-                     // the steps completed, one spare (never set), then per grid
-                     // the tiles done with the diagnostics step (batch_nctr ints)
+                     // the steps completed, one spare (never set), per grid the
+                     // tiles done with the diagnostics step, per step of the
+                     // launch (up to PERSIST_STEP_CAP) the tiles done with it
     int ctr_sel;     // the set the next multi-step launch uses (the other is zero)
+    int stall_tile;  // fault injection: the tile made to wait (else -1)
     int *d_err;      // set by a wait that timed out
     int persist_cap; // tiles d_nbr and d_ctr hold
     // fused diagnostics
@@ -1079,15 +1081,18 @@ int batch_build_nbr(lbm_batch *b, const BatchTile *h, int count, int width, int 
         b->d_ctr = nullptr;
         b->persist_cap = 0;
         if (grow((void **)&b->d_nbr, &cap_nbr, count * stride, sizeof(int)) ||
-            grow((void **)&b->d_ctr, &cap_ctr, 2 * (count + 5 + b->n), sizeof(int))) {
+            grow((void **)&b->d_ctr, &cap_ctr, 2 * (count + 5 + b->n + PERSIST_STEP_CAP),
+                 sizeof(int))) {
             free(nb);
             return LBM_ERR_OOM;
         }
         b->persist_cap = count;
     }
     // both counter sets start at zero; each launch zeroes the other one
-    cudaError_t e = cudaMemset(b->d_ctr, 0, 2 * ((size_t)count + 5 + b->n) * sizeof(int));
+    cudaError_t e =
+        cudaMemset(b->d_ctr, 0, 2 * ((size_t)count + 5 + b->n + PERSIST_STEP_CAP) * sizeof(int));
     b->ctr_sel = 0;
+    b->stall_tile = -1;
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_nbr, nb, (size_t)count * stride * sizeof(int), cudaMemcpyHostToDevice);
     free(nb);
@@ -1310,7 +1315,8 @@ long long next_diag(const lbm_batch *b, long long t)
 int batch_run_persistent(lbm_batch *b, int n)
 {
     const int prec = b->precision == LBM_FP64 ? 0 : 1;
-    const int cap = (int)((0x7fffffff - 1) / (b->ntiles > 0 ? b->ntiles : 1));
+    int cap = (int)((0x7fffffff - 1) / (b->ntiles > 0 ? b->ntiles : 1));
+    if (cap > PERSIST_STEP_CAP) cap = PERSIST_STEP_CAP;
     int left = n;
     while (left > 0) {
         const long long t = b->ctx[0]->step;
@@ -1332,12 +1338,14 @@ int batch_run_persistent(lbm_batch *b, int n)
         pa.parity0 = b->ctx[0]->cur;
         pa.nsteps = m;
         pa.diag_k = diag_k;
-        const size_t nctr = (size_t)b->ntiles + 5 + b->n;  // ints per counter set
+        const size_t nctr = (size_t)b->ntiles + 5 + b->n + PERSIST_STEP_CAP;  // per counter set
         pa.ctr = b->d_ctr + (size_t)b->ctr_sel * nctr;
         pa.ctr_next = b->d_ctr + (size_t)(b->ctr_sel ^ 1) * nctr;
         pa.nctr = (int)nctr;
         pa.flags = pa.ctr + 4;
         pa.case_ctr = pa.flags + b->ntiles + 1;
+        pa.step_done = pa.case_ctr + b->n;
+        pa.stall_tile = b->stall_tile;
         pa.err = b->d_err;
         pa.err_host = &b->d_status->err;
         pa.partials = b->d_partials;
@@ -1754,11 +1762,13 @@ int lbm_batch_debug_stall(lbm_batch *b, int tile)
     if (!b || tile < 0 || tile >= b->ntiles || !b->persist || !b->persist_ok)
         return LBM_ERR_INVALID_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ERR_CUDA;
-    // one neighbour: the spare counter after the tiles' own (index ntiles)
+    // one neighbour: the spare counter after the tiles' own (index ntiles);
+    // the tile always waits (no step-completion shortcut)
     const int rec[2] = {1, b->ntiles};
     if (cudaMemcpy(b->d_nbr + (size_t)tile * (PERSIST_NBMAX + 1), rec, sizeof rec,
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return LBM_ERR_CUDA;
+    b->stall_tile = tile;
     return LBM_OK;
 }
 

@@ -191,6 +191,7 @@ cudaError_t d2q9_batch_reduce(int precision, const DiagPartial *partials, const 
 
 // Several time steps of a batch in one cooperative launch (a queue of
 // (step, tile) pairs; see d2q9_batch_persist_kernel).
+constexpr int PERSIST_STEP_CAP = 1024;  // steps per multi-step launch (longer runs split)
 constexpr int PERSIST_NBMAX = 16;
 struct PersistArgs {
     const BatchCase *cases;
@@ -203,11 +204,14 @@ struct PersistArgs {
     int diag_k;        // step of the launch that carries the diagnostics, or -1
     int *ctr;          // 4 counters, then flags (= ctr + 4): ntiles + 1 step
                        // counters, then case_ctr (= flags + ntiles + 1):
-                       // ncases counters; nctr ints, all zero at the launch
+                       // ncases counters, then step_done (= case_ctr + ncases):
+                       // PERSIST_STEP_CAP counters; nctr ints, all zero at the launch
     int *ctr_next;     // the next launch's set of nctr ints, zeroed by this one
     int nctr;
     int *flags;
     int *case_ctr;     // per grid: tiles done with the diagnostics step
+    int *step_done;    // per step of the launch: tiles done with it
+    int stall_tile;    // fault injection: this tile always waits (else -1)
     int *err;          // device word set by a wait that timed out (never cleared here)
     int *err_host;     // mapped host word set with it (may be null)
     DiagPartial *partials;  // ntiles

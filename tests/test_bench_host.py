@@ -90,17 +90,20 @@ def test_diag_cadence_puts_one_diagnostics_step_in_every_timed_region():
 
 
 @pytest.mark.parametrize("t0,k,de", [(5, 20, 20), (0, 20, 20), (5, 2000, 100), (3, 7, 3),
-                                     (0, 1, 1), (17, 40, 100)])
+                                     (0, 1, 1), (17, 40, 100), (0, 2000, 5000), (7, 3000, 1500)])
 def test_multi_step_launch_count_holds_one_diagnostics_step_each(t0, k, de):
     """Re-derive the launch split by brute force: walk the steps, start a new
     launch whenever the current one already holds a diagnostics step and the
-    next step carries another."""
-    launches, has_diag = 1, False
+    next step carries another, or already holds STEP_CAP (1024) steps."""
+    launches, has_diag, n = 1, False, 0
     for t in range(t0, t0 + k):
+        if n == 1024 or (t % de == 0 and has_diag):
+            launches += 1
+            has_diag, n = False, 0
         if t % de == 0:
-            if has_diag:
-                launches += 1
             has_diag = True
+        n += 1
+    assert bench.STEP_CAP == 1024
     assert bench.launches_multi_step(t0, k, de) == launches
 
 
