@@ -187,7 +187,10 @@ int lbm_step(lbm_ctx *ctx, int n);
 
 /* Macroscopic fields at the current time (FP64 outputs): phi[N], p[N]
  * (hydrodynamic pressure), u[D*N] ([D][N]), mu[N].  Any output may be NULL.
- * on_device = 0: host arrays (the call synchronises the stream);
+ * on_device = 0: host arrays (the call synchronises the stream); when every
+ * given array is pinned host memory (cudaHostAlloc, cudaHostRegister), the
+ * pass writes them directly through their device addresses, else it writes
+ * a device staging buffer (allocated on the first such call) and copies;
  * on_device = 1: device arrays (asynchronous).  Errors: STATE, CUDA. */
 int lbm_moments(lbm_ctx *ctx, double *phi, double *p, double *u, double *mu,
                 int on_device);

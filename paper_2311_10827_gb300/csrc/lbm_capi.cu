@@ -58,6 +58,7 @@ struct lbm_ctx {
     cudaStream_t stream;
     cudaStream_t cap;    // private stream used for graph capture
     cudaEvent_t diag_ev; // recorded after a fused diagnostics copy
+    cudaEvent_t up_ev;   // recorded after lbm_init_phi's upload from host memory
     int diag_pending;
     long long last_diag_step;
     int has_last_diag;
@@ -281,6 +282,7 @@ void free_all(lbm_ctx *c)
         if (p) cudaFree(p);
     if (c->hres) cudaFreeHost(c->hres);
     if (c->diag_ev) cudaEventDestroy(c->diag_ev);
+    if (c->up_ev) cudaEventDestroy(c->up_ev);
     if (c->cap) cudaStreamDestroy(c->cap);
 }
 
@@ -463,7 +465,8 @@ int create_impl(const lbm_grid *grid, int lattice, const lbm_params *params, voi
     if (!oom && cudaMallocHost((void **)&ctx->hres, 2 * sizeof(DiagPartial)) != cudaSuccess)
         oom = true;
     if (!oom && (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
-                 cudaEventCreateWithFlags(&ctx->diag_ev, cudaEventDisableTiming) != cudaSuccess))
+                 cudaEventCreateWithFlags(&ctx->diag_ev, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&ctx->up_ev, cudaEventDisableTiming) != cudaSuccess))
         oom = true;
     if (oom) {
         cudaGetLastError();  // clear the allocation error
@@ -501,6 +504,7 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
         // 4-byte or 19 N 2-byte values, 256-byte aligned)
         double *stage = static_cast<double *>(ctx->f[1]);
         CK(cudaMemcpyAsync(stage, phi, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaEventRecord(ctx->up_ev, ctx->stream));
         src = stage;
     }
     if (int rc = set_eq_shift(ctx, 0.0f)) return rc;
@@ -519,7 +523,7 @@ int lbm_init_phi(lbm_ctx *ctx, const double *phi, int on_device)
                       ctx->S, ctx->stream);
     }
     // a host array is read until the upload completes: return after it
-    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && !on_device) e = cudaEventSynchronize(ctx->up_ev);
     CK(e);
     ctx->cur = 0;
     ctx->step = 0;
@@ -599,6 +603,31 @@ int lbm_moments(lbm_ctx *ctx, double *phi, double *p, double *u, double *mu, int
     if (ctx->err == LBM_ERR_CUDA) return LBM_ERR_CUDA;
     const size_t N = (size_t)ctx->N;
     if (on_device) return run_pass(ctx, PASS_MACROS, ctx->stream, phi, p, u, mu);
+    // Host arrays in pinned (page-locked, device-mapped) memory: the pass
+    // writes them directly through their device addresses, with no staging
+    // buffer and no separate copies; it returns once they are written.
+    {
+        double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+        double *const host[4] = {phi, p, u, mu};
+        bool mapped = true;
+        for (int k = 0; k < 4 && mapped; ++k) {
+            if (!host[k]) continue;
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, host[k]) != cudaSuccess ||
+                at.type != cudaMemoryTypeHost || !at.devicePointer) {
+                cudaGetLastError();
+                mapped = false;
+            } else {
+                dev[k] = static_cast<double *>(at.devicePointer);
+            }
+        }
+        if (mapped) {
+            int rc = run_pass(ctx, PASS_MACROS, ctx->stream, dev[0], dev[1], dev[2], dev[3]);
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(ctx->stream));
+            return LBM_OK;
+        }
+    }
     if (!ctx->stage) CK(cudaMalloc((void **)&ctx->stage, (3 + ctx->D) * N * sizeof(double)));
     double *s_phi = ctx->stage, *s_p = s_phi + N, *s_mu = s_p + N, *s_u = s_mu + N;
     int rc = run_pass(ctx, PASS_MACROS, ctx->stream, phi ? s_phi : nullptr, p ? s_p : nullptr,
