@@ -965,9 +965,13 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int *p)
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_gpu(int *p, int v)
+__device__ __forceinline__ void st_relaxed_gpu(int *p, int v)
 {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 // Longest wait of a tile for its neighbours, in SM clock cycles (about 2 s):
@@ -1084,9 +1088,10 @@ __global__ void __launch_bounds__(RG) d2q9_batch_reduce_kernel(const DiagPartial
 // other tiles write during the launch is read from L2 only: by the bulk
 // row-segment copies (the copy engine reads L2) or, on the register path,
 // by ld.global.cg.  The writer CTA stores, passes bar.sync, and its thread 0
-// fences and does st.release.gpu on the tile's counter; a polling lane of
-// the reader does ld.acquire.gpu, observes the count, fences, and the CTA
-// passes bar.sync before any copy or load of the next step is issued; a
+// executes fence.acq_rel.gpu and writes the tile's counter (relaxed: fence
+// and write form a release); a polling lane of the reader does
+// ld.acquire.gpu, observes the count, fences, and the CTA passes bar.sync
+// before any copy or load of the next step is issued; a
 // thread that issues bulk copies first executes fence.proxy.async.global,
 // which orders what it has observed through ordinary loads before its
 // copy-engine reads.  No read of this launch's data goes through L1.
@@ -1275,9 +1280,13 @@ __global__ void __launch_bounds__((Occ<T, PASS_STATE, TX>::nth), (Occ<T, PASS_ST
         // final step (then every pair is done) records the final shift, after
         // every reduction.
         const bool last_steps = k == pa.diag_k || k == pa.nsteps - 1;
+        // One release fence, then the counters as relaxed writes and atomics
+        // (each a release pattern): the barrier above orders every thread's
+        // stores of the tile before the fence.  A fence followed by a release
+        // store (two fences) cost about 3% of a step.
         if (lin == 0) {
-            __threadfence();
-            st_release_gpu(pa.flags + ti, k + 1);
+            fence_acq_rel_gpu();
+            st_relaxed_gpu(pa.flags + ti, k + 1);
             atomicAdd(pa.step_done + k, 1);  // the step's completion count
             if (last_steps) {
                 int fl = 0;
