@@ -365,7 +365,11 @@ int lbm_batch_set_shape(lbm_batch *b, int width, int rows);
  * barrier and no launch per step, any number of tiles fits (a batch of many
  * grids walks its tile list every step), and tiles of the next step start
  * while the last ones of a step still run.  The results are the same, bit
- * for bit, as those of per-step launches.  A wait is bounded (about 2 s of
+ * for bit, as those of per-step launches, except after a fused diagnostics
+ * step that moves the FP32 equilibrium shift inside a launch (the launch
+ * writes with the new shift from its next launch on, per-step launches from
+ * the next step on; the two differ by rounding).  A launch holds at most
+ * 1024 steps (longer calls are split).  A wait is bounded (about 2 s of
  * SM clock).  On a timeout the tile sets an error word, fills its region of
  * the rest population (both buffers) and of S with NaN (so that diagnostics
  * report non-finite fields) and stops; the launch then ends, lbm_batch_step

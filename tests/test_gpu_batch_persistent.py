@@ -103,6 +103,36 @@ def test_multistep_walks_more_tiles_than_resident_ctas(gpu):
     assert_same(run_pair(gpu, small, "fp64", 64, 8, (5, 2)))
 
 
+def test_long_call_splits_into_launches_of_at_most_1024_steps(gpu):
+    """A call of more steps than one multi-step launch holds (1024, the size
+    of the per-step completion counts) is split into launches of 1024 and 76
+    steps; the state equals that of per-step launches bit for bit (FP32,
+    staged pulls).  Without fused diagnostics: a diagnostics step inside a
+    multi-step launch moves the FP32 equilibrium shift from the next launch
+    on, per-step launches from the next step on, and the two differ by
+    rounding (the shift is an exact symmetry of the step only in exact
+    arithmetic)."""
+    cases = [((128, 64), dict(BASE, rho_l=10.0), wl.droplet(128, 64, 15.0, 4.0)),
+             ((128, 48), dict(BASE, rho_l=50.0), wl.droplet(128, 48, 12.0, 4.0))]
+    batches = [gpu.Batch([(sh, prm) for sh, prm, _ in cases], precision="fp32") for _ in range(2)]
+    try:
+        for b in batches:
+            for i, (_, _, phi) in enumerate(cases):
+                b.case(i).init_phi(phi)
+            b.set_shape(64, 16)
+        batches[1].set_persistent(True)
+        for b in batches:
+            b.step(1100)
+        assert batches[1].persistent(read_timeout=True)[1] is False
+        for i in range(len(cases)):
+            assert batches[1].case(i).t == 1100
+            for x, y in zip(batches[0].case(i).get_state(), batches[1].case(i).get_state()):
+                assert np.array_equal(x, y)
+    finally:
+        for b in batches:
+            b.close()
+
+
 def _start_at(b, cases, t0):
     """Every grid initialised from its phi0 (Eq. H_i initial condition), then
     set to time t0 (the state unchanged): the diagnostics cadence counts from
