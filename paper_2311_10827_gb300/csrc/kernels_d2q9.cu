@@ -19,8 +19,8 @@
 // by L2).  A thread's own output row was summed into phi by the same thread
 // one iteration earlier, so its nine pulled f values stay in registers.
 // The pulls are loaded by each thread into registers, or (the FP32
-// multi-step kernel) staged in shared memory one iteration ahead as 16-byte
-// copies of whole row segments.
+// multi-step kernel) staged in shared memory one iteration ahead by bulk
+// asynchronous copies of whole row segments.
 // Row tiles march in alternating directions (even tiles down, odd tiles up),
 // so two neighbouring tiles reach their shared boundary rows at the same
 // time and the y-halo rows are served from L2 instead of being re-read from
@@ -203,7 +203,8 @@ __device__ __forceinline__ void warp_reduce(double &sum0, double &sum1, T &mx, T
 
 // Resident CTAs per SM targeted by the register budget: every FP32 variant
 // fits 64 registers (1024 threads per SM; the diagnostics accumulate in
-// shared memory); FP64 512 threads.
+// shared memory), with small register spills in the multi-step kernels
+// (measured: removing them did not change the step time); FP64 512 threads.
 template <typename T, int PASS, int TX>
 struct Occ {
     static constexpr int nth = TX * TYB;
@@ -258,8 +259,9 @@ struct SegLayout {
     static_assert(DACC + 11 * TX * TYB <= 2 * STAGE, "diagnostics layout");
 };
 
-// Per-thread diagnostics accumulators (a diagnostics pass runs the register
-// path and keeps them where the staging would be): the sums of phi,
+// Per-thread diagnostics accumulators, in the kernel's dynamic shared memory
+// (at its start on the register path, after the buffers of the staged
+// diagnostics layout): the sums of phi,
 // rho |u|^2 / 2, S and S_prev (FP64 for FP64 storage; for FP32 each as an
 // exact FP32 (hi, lo) pair, so that the FP32 step does no FP64 arithmetic per
 // node), then the extrema of |u|^2 and mu.
